@@ -1,0 +1,333 @@
+"""Benchmark of the DISK spatially varying filter on GB300.
+
+Step = one full pass of the hot path over one synthetic frame: 3840 x 2160
+RGB, FP16 storage, FP32 arithmetic, 8 x 8 basis of fitted ellipse complexes
+(L=4 layers x T=24 taps), two smooth per-pixel parameter maps; per pixel the
+Eq. 9 interpolation of all L x T taps and the L cascaded bilinear layers.
+
+Prints one JSON line (rank 0).  value = frames' pixels / device time (Gpix/s),
+summed over ranks (replicas only: every rank filters its own frame).
+--impl reference times the FP64 CPU oracle on bounded crops of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2512_04556_gb300 import workloads as wl  # noqa: E402
+
+BASES = os.path.join(ROOT, "tests", "golden", "bases")
+C4_BASIS = os.path.join(BASES, "ellipse8x8_L4T24.dkb")
+BYTES_PER_PX = 20.0   # fused-pass algorithmic bytes: in 6 + out 6 + 2 maps x 4
+NOMINAL_HBM_GBS = 8000.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="disk", choices=["disk", "reference"])
+    p.add_argument("--no-extras", action="store_true", help="skip dense/e2e/cpu extras")
+    return p.parse_args()
+
+
+def dist_init(n):
+    if n <= 1 and "WORLD_SIZE" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, world, dist
+
+
+def c4_inputs():
+    H, W = wl.C4["H"], wl.C4["W"]
+    img = wl.to_fp16(wl.image_rects(H, W, 3))
+    m0 = wl.param_map(H, W, *wl.C4["map_range0"], sigma=wl.C4["map_sigma"], stream=0)
+    m1 = wl.param_map(H, W, *wl.C4["map_range1"], sigma=wl.C4["map_sigma"], stream=1)
+    return img, np.stack([m0, m1])
+
+
+class Clocks:
+    """nvidia-smi sampler running while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.rows, self.proc = gpu, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def run_disk(args, rank, world, dist):
+    import torch
+
+    from paper_2512_04556_gb300 import disk
+
+    dev = torch.cuda.current_device()
+    H, W = wl.C4["H"], wl.C4["W"]
+    img, maps = c4_inputs()
+    basis = disk.Basis.load(C4_BASIS)
+    d_img = torch.from_numpy(img).cuda()
+    d_maps = torch.from_numpy(maps).cuda()
+    d_out = torch.empty_like(d_img)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        disk.sv_filter(basis, d_img, d_maps, out=d_out, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(dev) as clk:
+        t0 = time.perf_counter()
+        for i in range(K):
+            flush.fill_(i & 0xFF)          # evict the frame from L2 between steps
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    px = H * W
+    value = world * px / (ms * 1e-3) / 1e9
+    res = {"ms_per_step": ms, "value": value, "clocks": clk.summary(), "wall_s": wall,
+           "gpu_launches": K * basis.L, "step_ms_min": float(np.min(step_ms)),
+           "step_ms_median": float(np.median(step_ms))}
+    if rank == 0 and not args.no_extras:
+        res.update(extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream))
+    return res
+
+
+def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
+    import torch
+
+    from paper_2512_04556_gb300 import disk
+    H, W = wl.C4["H"], wl.C4["W"]
+    px = H * W
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = json.load(open(pk))
+    hbm = peaks.get("hbm_gbs")
+    out = {}
+    achieved = BYTES_PER_PX * px / (ms * 1e-3) / 1e9
+    out["roofline"] = {
+        "bound": "hbm", "achieved": achieved, "peak": hbm or 6800.0, "unit": "GB/s",
+        "frac": achieved / (hbm or 6800.0), "peak_source": "measured" if hbm else "fallback",
+        "frac_of_nominal_8tb": achieved / NOMINAL_HBM_GBS, "traffic": None,
+        "kernel": "sv_layer_kernel (all L launches of one pass)",
+        "bytes_per_px": BYTES_PER_PX}
+    # shared-memory bound model: every tap reads four 16-byte corners
+    taps = basis.L * basis.T
+    smem_bytes = px * taps * 4 * 16
+    out["smem_model"] = {"bytes_per_pass": smem_bytes, "achieved_gbs": smem_bytes / (ms * 1e-3) / 1e9}
+
+    # end to end through the public API with pinned host buffers
+    h_img = torch.from_numpy(img).pin_memory()
+    h_maps = torch.from_numpy(maps).pin_memory()
+    h_out = torch.empty_like(h_img).pin_memory()
+    n = 20
+    for _ in range(3):
+        d_img.copy_(h_img, non_blocking=True)
+        d_maps.copy_(h_maps, non_blocking=True)
+        disk.sv_filter(basis, d_img, d_maps, out=d_out, stream=stream)
+        h_out.copy_(d_out, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        d_img.copy_(h_img, non_blocking=True)
+        d_maps.copy_(h_maps, non_blocking=True)
+        disk.sv_filter(basis, d_img, d_maps, out=d_out, stream=stream)
+        h_out.copy_(d_out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / n
+    out["e2e"] = {"value": px / (e2e_ms * 1e-3) / 1e9, "unit": "Gpix/s",
+                  "h2d_bytes_per_step": int(h_img.numel() * 2 + h_maps.numel() * 4),
+                  "d2h_bytes_per_step": int(h_out.numel() * 2), "ms_per_step": e2e_ms}
+
+    # dense spatially varying convolution on the same frame (Eq. 1 per pixel)
+    n0 = np.linspace(2.0, 40.0, 16)
+    n1 = np.linspace(0.0, 1.0, 16)
+    lut = torch.from_numpy(wl.ellipse_lut(n0, n1, 81)).cuda()
+    d_dense = torch.empty_like(d_img)
+    disk.dense_sv([n0, n1], lut, d_img, d_maps, out=d_dense, stream=stream)
+    torch.cuda.synchronize()
+    nd = 3
+    ts = []
+    for _ in range(nd):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        disk.dense_sv([n0, n1], lut, d_img, d_maps, out=d_dense, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    dms = float(np.mean(ts))
+    o = d_out.float()
+    dd = d_dense.float()
+    mse = float(((o - dd) ** 2).mean().item())
+    out["dense_sv"] = {"value": px / (dms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": dms,
+                       "kernel_max": "81x81", "lut": "16x16 ellipse grid",
+                       "speedup_disk_vs_dense": dms / ms,
+                       "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20)))}
+    return out
+
+
+def _oracle_crop(h, w):
+    from oracle import basis_io
+    H, W = wl.C4["H"], wl.C4["W"]
+    img, maps = c4_inputs()
+    axes, theta = basis_io.read(C4_BASIS)
+    y0, x0 = (H - h) // 2, (W - w) // 2
+    crop = np.ascontiguousarray(img[y0:y0 + h, x0:x0 + w].astype(np.float64))
+    cm = np.ascontiguousarray(maps[:, y0:y0 + h, x0:x0 + w].astype(np.float64))
+    nv = np.concatenate(axes).astype(np.float64)
+    return crop, cm, [len(a) for a in axes], nv, theta.astype(np.float64)
+
+
+def cpu_baseline(sample_px=(256, 256), budget_s=15.0):
+    """The FP64 oracle, as it stands, on a centre crop of the same frame,
+    repeated until budget_s of CPU time has passed."""
+    import oracle
+    h, w = sample_px
+    args = _oracle_crop(h, w)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.sv_filter(*args)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n * h * w / dt / 1e9, "unit": "Gpix/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} x centre crop {h}x{w} of the 3840x2160 frame, FP64, {dt:.1f} s"}
+
+
+def run_reference(args, base):
+    """Reference arm: the oracle on the host cores, one 128 x 128 centre crop
+    of the frame per step."""
+    import oracle
+    h = w = 128
+    crop = _oracle_crop(h, w)
+    for _ in range(args.warmup):
+        oracle.sv_filter(*crop)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sv_filter(*crop)
+    dt = time.perf_counter() - t0
+    v = args.steps * h * w / dt / 1e9
+    line = dict(base, impl="reference", value=v, ms_per_step=dt / max(args.steps, 1) * 1e3,
+                cpu_baseline={"value": v, "unit": "Gpix/s", "cores": oracle.num_threads(),
+                              "kind": "oracle",
+                              "sample": f"{args.steps} steps x centre crop {h}x{w}, FP64"},
+                e2e={"value": v, "unit": "Gpix/s", "h2d_bytes_per_step": 0,
+                     "d2h_bytes_per_step": 0})
+    line["dtype"] = "f64"
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, dist = dist_init(args.gpus)
+    base = {"metric": "SV-filter Gpix/s at 4K RGB (vs dense-SV; kernel fits/s to fixed MSE)",
+            "unit": "Gpix/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sv_filter_4k_rgb_fp16_2d", "H": wl.C4["H"], "W": wl.C4["W"],
+                       "C": 3, "storage": "fp16", "basis": "8x8 fitted ellipses",
+                       "L": wl.C4["L"], "T": wl.C4["T"], "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"}}
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, base)
+        if dist:
+            dist.destroy_process_group()
+        return
+    res = run_disk(args, rank, world, dist)
+    if rank == 0:
+        line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"],
+                    clocks=res["clocks"], gpu_launches=res["gpu_launches"])
+        for k in ("roofline", "e2e", "dense_sv", "smem_model"):
+            if k in res:
+                line[k] = res[k]
+        line["step_ms_min"] = res["step_ms_min"]
+        line["step_ms_median"] = res["step_ms_median"]
+        if not args.no_extras and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

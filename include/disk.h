@@ -1,0 +1,208 @@
+/*
+ * disk.h -- C ABI of libdisk.so: spatially varying filtering with a sparse
+ * kernel complex (DISK, "Differentiable Sparse Kernel Complex for Efficient
+ * Spatially-Variant Convolution", arXiv 2512.04556), GB300 (sm_103a) native.
+ *
+ * General rules for every entry point
+ *   - Status: 0 (DISK_OK) on success, a negative DISK_ERR_* code otherwise;
+ *     disk_error_string() names it.  Arguments are validated before any work
+ *     is queued; on an error nothing is launched and outputs are untouched.
+ *   - Pointers prefixed d_ are device pointers on the current CUDA device;
+ *     all other pointers are host pointers.  Every buffer is caller-owned;
+ *     the library owns only disk_basis handles and per-call scratch, which it
+ *     takes from the stream-ordered pool of the call's stream and returns on
+ *     the same stream.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on that stream; no entry point
+ *     synchronises the device except disk_basis_* (host<->device uploads).
+ *   - Images are interleaved H x W x C (C = 3 or 4), row pitch in BYTES,
+ *     element type DISK_F32 (float) or DISK_F16 (IEEE half).  Arithmetic is
+ *     FP32 throughout; FP16 is a storage type only (inputs widened exactly,
+ *     outputs rounded to nearest even).
+ *   - Offsets are in pixels, (dx, dy) = (column, row) direction.  A tap at a
+ *     fractional offset is sampled bilinearly with texel centres at integer
+ *     coordinates; image filtering clamps coordinates to the edge, impulse
+ *     synthesis treats everything outside its canvas as zero.
+ */
+#ifndef DISK_H
+#define DISK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DISK_OK = 0,
+  DISK_ERR_INVALID_ARG = -1,  /* bad shape, pitch, pointer, enum or value   */
+  DISK_ERR_BAD_FILE = -2,     /* basis file missing, truncated or corrupt   */
+  DISK_ERR_UNSUPPORTED = -3,  /* valid request outside the built limits     */
+  DISK_ERR_CUDA = -4,         /* a CUDA runtime call failed                 */
+  DISK_ERR_OOM = -5,          /* device or host allocation failed           */
+  DISK_ERR_TIMEOUT = -6       /* a bounded device-side wait expired         */
+};
+
+enum { DISK_F32 = 0, DISK_F16 = 1 };
+
+/* Library limits (validated at every entry point). */
+#define DISK_MAX_DIMS 2          /* kernel-space dimensions of a basis       */
+#define DISK_MAX_NODES_AXIS 64   /* basis nodes per kernel-space axis        */
+#define DISK_MAX_LAYERS 16       /* sparse layers L                          */
+#define DISK_MAX_TAPS 64         /* taps per layer T                         */
+#define DISK_MAX_REACH 40.0f     /* largest |dx|, |dy| of any basis tap, px   */
+
+/* Library version, major*10000 + minor*100 + patch. */
+int disk_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *disk_error_string(int status);
+
+/* Detail of the last failure on the calling thread (never NULL; valid until
+ * the thread's next failing call). */
+const char *disk_last_error_message(void);
+
+/* ---------------------------------------------------------------------------
+ * Basis of pre-optimised complexes (Sec. 4.3, Eq. 8).
+ *
+ * A basis samples a 1-D or 2-D kernel space at nodes p_1 < ... < p_n per
+ * axis (Eq. 8 orders them increasingly); node k holds one complex
+ * f_k = {(o_{k,l,i}, w_{k,l,i})}: L layers of T taps (Eq. 2, Eq. 5).
+ * theta layout: float [B][L][T][3] = (dx, dy, w), B = n_nodes[0] (1-D) or
+ * n_nodes[0] * n_nodes[1] (2-D, node (a, b) at index a * n_nodes[1] + b, axis
+ * 0 driven by map 0).  The handle keeps a host copy and a device copy on the
+ * device current at creation; it is immutable and may be shared by
+ * concurrent calls on any stream of that device.
+ * ------------------------------------------------------------------------- */
+typedef struct disk_basis disk_basis;
+
+/* Build a basis from host arrays.  node_vals holds n_nodes[0] values for
+ * axis 0 followed (2-D) by n_nodes[1] values for axis 1, each strictly
+ * increasing.  Every value must be finite and every |dx|, |dy| at most
+ * DISK_MAX_REACH.  Uploads synchronously.  *out receives a new handle. */
+int disk_basis_from_arrays(int dims, const int *n_nodes, const float *node_vals,
+                           int L, int T, const float *theta, disk_basis **out);
+
+/* Read a basis file (format: 8-byte magic "DISKBAS1", then little-endian
+ * uint32 version=1, dims, L, T, n_nodes[2] (n_nodes[1]=1 for 1-D), float32
+ * node values, float32 theta, and a trailing uint64 FNV-1a hash of all
+ * preceding bytes).  DISK_ERR_BAD_FILE on any mismatch. */
+int disk_basis_load(const char *path, disk_basis **out);
+
+/* Write the basis in the format disk_basis_load reads. */
+int disk_basis_save(const disk_basis *basis, const char *path);
+
+/* Shape of a basis; any output pointer may be NULL. */
+int disk_basis_info(const disk_basis *basis, int *dims, int *n_nodes2, int *L,
+                    int *T);
+
+/* Release a handle (NULL is a no-op).  The caller ensures no queued call
+ * still uses it. */
+void disk_basis_free(disk_basis *basis);
+
+/* ---------------------------------------------------------------------------
+ * Spatially varying filter (Sec. 4.3 Eq. 9 + Sec. 3.2 Eq. 3).
+ *
+ * For every output pixel x, alpha(x) are the linear (1-D) or bilinear (2-D)
+ * interpolation weights of the map value(s) p(x) between the bracketing
+ * nodes (p clamped to the node range; a non-finite p acts as the first
+ * node), the pixel's complex is sum_k alpha_k(x) f_k applied to offsets and
+ * weights alike (Eq. 9), and the L layers are applied in cascade (Eq. 3):
+ *   I_l[x] = sum_i w_{l,i}(x) * bilinear(I_{l-1}, x + o_{l,i}(x)),
+ * every layer using the parameters interpolated at its own output pixel.
+ *
+ * d_in / d_out: H x W x C images of type dtype with row pitches in bytes
+ *   (multiples of the element size, at least W*C*elem).  d_in and d_out must
+ *   not overlap.
+ * d_maps: float [dims][H][W], dense, raw parameter values.
+ * Limits: 1 <= H, W <= 32768; C in {3, 4}.
+ * Scratch: 2 * H * W * 16 bytes (L >= 3) or H * W * 16 bytes (L = 2) from
+ *   the stream's pool for the intermediate layers, freed on the stream. */
+int disk_sv_filter(const disk_basis *basis, const void *d_in, size_t in_pitch,
+                   void *d_out, size_t out_pitch, int H, int W, int C,
+                   int dtype, const float *d_maps, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Dense spatially varying convolution (Sec. 3.1 Eq. 1 per pixel), the
+ * reference DISK approximates and its speed baseline:
+ *   out[x] = sum_m K_x[m] * I[clamp(x - m)],  K_x = sum_k alpha_k(x) D_k,
+ * with the same alpha(x) as disk_sv_filter over the dense node kernels D_k.
+ * The x - m indexing is true convolution, which is what a fitted complex
+ * reproduces (its impulse response is its gather stencil reflected).
+ * d_lut: float [B][Kd][Kd] node kernels (Kd odd, centre (Kd-1)/2, Kd <= 85),
+ *   node order as for a basis.  Other arguments as disk_sv_filter.  No
+ *   scratch. */
+int disk_dense_sv(int dims, const int *n_nodes, const float *node_vals,
+                  const float *d_lut, int Kd, const void *d_in, size_t in_pitch,
+                  void *d_out, size_t out_pitch, int H, int W, int C,
+                  int dtype, const float *d_maps, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Impulse-response synthesis (Sec. 4.4 Eq. 10; the composite of Eq. 4).
+ *
+ * For each of `batch` shift-invariant complexes d_theta [batch][L][T][3]
+ * (pixels), the response to a unit impulse at the centre of a zero-padded
+ * plane (nothing is truncated), cropped to K x K about the centre, into
+ * d_out [batch][K][K] (float).  K odd, 1 <= K <= 257.  max_reach (<= 256)
+ * bounds every |dx|, |dy| of d_theta and sizes the canvases; a complex with a
+ * tap beyond it (or a non-finite value) gets NaN in every output element.
+ * Scratch: 2 * batch canvases of side 2 * ((K-1)/2 + L*(ceil(max_reach)+1)
+ * + 1) + 1 floats from the stream's pool. */
+int disk_synth_kernel(const float *d_theta, int batch, int L, int T, int K,
+                      float max_reach, float *d_out, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Differentiable fit (Sec. 4.1 Eq. 4-5): for each of `batch` dense targets,
+ * the complex theta minimising the loss between its impulse response
+ * (Eq. 10) and the target, by Adam (beta 0.9/0.999, eps 1e-8) with the
+ * learning rate decayed linearly from lr0 to lr1 over `steps` (Sec. 5.1).
+ *
+ * d_targets: the batch's targets packed back to back, target b a float
+ *   [K_b][K_b] block (K_b = sizes[b], odd, <= 257, centre (K_b-1)/2).
+ * sizes: host int[batch].
+ * loss: DISK_LOSS_MSE = sum over the plane of (K_syn - K_tgt)^2 / K^2 with
+ *   the target zero-padded; DISK_LOSS_CHARB = sum of (sqrt(d^2 + eps^2) - eps)
+ *   / K^2 (Charbonnier, Eq. 11; eps > 0).
+ * init: DISK_INIT_GIVEN (d_theta_io holds the start), DISK_INIT_IR (Eq. 6,
+ *   ring step matching the target's second moment), DISK_INIT_SS (Sec. 4.2:
+ *   layer 1 from dart throwing over the target's non-zero pixels with the
+ *   Eq. 7 radius, SplitMix64 seeded with `seed`; later layers Eq. 6 rings),
+ *   DISK_INIT_RAND (offsets uniform in +-(K-1)/(2L), SplitMix64).
+ * Offsets are optimised in units of s_b = max(1, (K_b-1)/2) and clamped to
+ * |o| <= s_b per axis (from the start, whatever the init); weights are raw.
+ * d_theta_io: float [batch][L][T][3] (pixels): start (GIVEN) and result.
+ * d_final_loss: float [batch], loss at the result (may be NULL).
+ * d_loss_hist: float [batch][steps+1], loss before every step and after the
+ *   last (may be NULL).
+ * Limits: L * T <= 512.  Launches: a plan upload (per-target offsets carried
+ * in kernel parameters, one launch per 512 targets), one init kernel (unless
+ * GIVEN) and one persistent kernel, one CTA per target, largest targets
+ * first.  Never synchronises, so a call can be captured in a CUDA graph.
+ * Scratch:
+ * (L+3) canvases of side 2*max((K_b-1)/2, (L+1)*(ceil(s_b)+1))+3 per target
+ * from the stream's pool. */
+enum { DISK_LOSS_MSE = 0, DISK_LOSS_CHARB = 1 };
+enum { DISK_INIT_GIVEN = 0, DISK_INIT_IR = 1, DISK_INIT_SS = 2, DISK_INIT_RAND = 3 };
+
+int disk_fit(const float *d_targets, const int *sizes, int batch, int L, int T,
+             int steps, float lr0, float lr1, int init, int loss, float eps,
+             uint64_t seed, float *d_theta_io, float *d_final_loss,
+             float *d_loss_hist, void *stream);
+
+/* One evaluation of the fit objective and its gradient (the hand-written
+ * backward of the cascade: d/dw, d/ddx, d/ddy of every tap, through the
+ * adjoint of each layer), at d_theta [batch][L][T][3] (pixels, offsets
+ * clamped to |o| <= s_b as in disk_fit), into d_loss [batch] and
+ * d_grad [batch][L][T][3] (pixel units).  Other arguments as disk_fit.  At an
+ * exact integer offset the derivative is the one-sided one of the floor
+ * convention (fraction in [0, 1)). */
+int disk_fit_loss_grad(const float *d_targets, const int *sizes, int batch, int L,
+                       int T, int loss, float eps, const float *d_theta,
+                       float *d_loss, float *d_grad, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DISK_H */

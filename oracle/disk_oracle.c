@@ -514,8 +514,8 @@ void orc_init_rand(int K, int L, int T, uint64_t seed, double *theta) {
 /* Differentiable fit, Eq. 4: Adam (Kingma & Ba 2015; beta1 0.9, beta2 0.999, */
 /* eps 1e-8) with the learning rate decayed linearly from lr0 to lr1 over the */
 /* steps (Sec. 5.1).  Offsets are optimised in units of the target's half-    */
-/* width s = max(1, (K-1)/2) and clamped to |o/s| <= 1 per axis after each    */
-/* step; weights are optimised raw.  init: 0 given (theta_io), 1 radial,      */
+/* width s = max(1, (K-1)/2) and clamped to |o/s| <= 1 per axis at the start  */
+/* and after each step; weights are optimised raw.  init: 0 given (theta_io), 1 radial,      */
 /* 2 sparse sampling, 3 random.  loss_hist[steps+1] (if non-NULL) receives    */
 /* the loss before every step and after the last.                            */
 /* ------------------------------------------------------------------------- */
@@ -531,7 +531,11 @@ int orc_fit(const double *tgt, int K, int L, int T, int steps, double lr0,
   if (s < 1.0) s = 1.0;
   double *m = (double *)calloc(P, sizeof(double)), *v = (double *)calloc(P, sizeof(double));
   double *g = (double *)malloc(sizeof(double) * P), *q = (double *)malloc(sizeof(double) * P);
-  for (int j = 0; j < P; j++) q[j] = (j % 3 == 2) ? theta_io[j] : theta_io[j] / s;
+  /* the canvas bound |o/s| <= 1 holds from the first step, whatever the init */
+  for (int j = 0; j < P; j++) {
+    q[j] = (j % 3 == 2) ? theta_io[j] : theta_io[j] / s;
+    if (j % 3 != 2) { if (q[j] > 1.0) q[j] = 1.0; if (q[j] < -1.0) q[j] = -1.0; }
+  }
   const double b1 = 0.9, b2 = 0.999, aeps = 1e-8;
   double b1t = 1.0, b2t = 1.0;
   for (int t = 0; t < steps; t++) {

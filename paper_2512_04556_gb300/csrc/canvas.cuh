@@ -1,0 +1,68 @@
+// Device building blocks for shift-invariant complexes on a zero-padded
+// square canvas (impulse synthesis, Sec. 4.4 Eq. 10, and its adjoint for the
+// fit).  A canvas of half-width R is a dense (2R+1)^2 float plane centred on
+// c = (R, R).  All routines are executed by every thread of one CTA.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sv_common.cuh"
+
+namespace disk {
+
+// Per-layer bookkeeping derived from the current taps: H_l = ceil(reach)+1,
+// support half-width S_l = H_1 + ... + H_l of the layer's output.
+struct LayerExtent {
+  int H;
+  int S;
+};
+
+// Zero the square frame b_in < max(|dx|,|dy|) <= b_out of a canvas.
+__device__ __forceinline__ void zero_frame(float *plane, int R, int b_in, int b_out) {
+  b_out = min(b_out, R);
+  if (b_out <= b_in) return;
+  const int side = 2 * b_out + 1, N = 2 * R + 1;
+  for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
+    const int v = j / side - b_out, u = j % side - b_out;
+    if (max(abs(u), abs(v)) > b_in) plane[(R + v) * N + (R + u)] = 0.f;
+  }
+}
+
+// floor split of an offset: d = n + f, n = floor(d), f in [0, 1).  The fit
+// uses this exact convention (as the oracle does) because the one-sided
+// derivative taken at integer offsets depends on it.
+__device__ __forceinline__ int split_floor(float d, float &f) {
+  const float fl = floorf(d);
+  f = d - fl;
+  return __float2int_rn(fl);
+}
+
+// One shift-invariant layer (Eq. 3) with the tap set taps[T] (dx, dy, w):
+// dst[p] = sum_i w_i * bilinear(src, p + o_i) for every p with
+// max(|p - c|) <= b.  src must hold the true values (zeros outside the
+// support) on the box of half-width b + halo; halo bounds every tap's reach
+// as ceil(reach) + 1.  sign = -1 applies the taps at -o (the adjoint of a
+// layer on a zero-bounded canvas, by the symmetry of the bilinear tent).
+__device__ __forceinline__ void canvas_layer(const float *src, float *dst, int R, int b,
+                                             const float4 *taps, int T, int halo, float sign) {
+  const int side = 2 * b + 1, N = 2 * R + 1;
+  for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
+    const int v = j / side - b, u = j % side - b;
+    const float *base = src + (R + v) * N + (R + u);
+    float acc = 0.f;
+    for (int i = 0; i < T; ++i) {
+      const float4 t = taps[i];
+      float fx, fy;
+      const int nx = min(max(split_floor(sign * t.x, fx), -halo), halo - 1);
+      const int ny = min(max(split_floor(sign * t.y, fy), -halo), halo - 1);
+      const float *q = base + ny * N + nx;
+      const float c00 = q[0], c01 = q[1], c10 = q[N], c11 = q[N + 1];
+      const float wy1 = t.z * fy, wy0 = t.z - wy1;
+      const float w11 = wy1 * fx, w10 = wy1 - w11, w01 = wy0 * fx, w00 = wy0 - w01;
+      acc += w00 * c00 + w01 * c01 + w10 * c10 + w11 * c11;
+    }
+    dst[(R + v) * N + (R + u)] = acc;
+  }
+}
+
+}  // namespace disk

@@ -1,0 +1,541 @@
+// Differentiable fit of sparse complexes to dense targets (Sec. 4.1 Eq. 4-6,
+// Sec. 4.2 Eq. 7, Sec. 4.4 Eq. 10-11, schedule of Sec. 5.1), batched over
+// targets of uneven size in one persistent launch.
+//
+// One CTA owns one target for all steps (targets ordered largest first, so
+// the block scheduler runs them longest-processing-time first).  Per step:
+//   forward   impulse on a zero-padded canvas, L shift-invariant layers, each
+//             computed only on its support box S_l = H_1 + ... + H_l, with
+//             H_l = ceil(max |o_l|) + 1 from the current taps;
+//   loss      MSE (or Charbonnier, Eq. 11) over the plane, target zero-padded;
+//   backward  dL/dI_L, then per layer the tap gradients (one warp per tap,
+//             warp-shuffle reductions) and the adjoint plane, which on a
+//             zero-bounded canvas is the same layer applied at -o (the
+//             bilinear tent is symmetric) -- a gather, no atomics;
+//   update    Adam with linearly decayed lr on offsets in units of the target
+//             half-width s (clamped to |o/s| <= 1) and raw weights.
+// All L+1 activations stay in a per-target scratch region (L2-resident for
+// all but the largest targets); the canvas half-width bounds every support
+// the clamp allows.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "canvas.cuh"
+
+namespace disk {
+namespace {
+
+constexpr int kFitThreads = 512;
+constexpr int kFitWarps = kFitThreads / 32;
+
+struct FitMeta {
+  long long tgt_off;     // floats into the packed targets
+  long long canvas_off;  // floats into scratch
+  long long idx_off;     // ints into the index scratch (sparse-sampling init)
+  int K, R;
+  float s;               // offset scale: max(1, (K-1)/2)
+};
+
+struct FitArgs {
+  const float *targets;
+  const FitMeta *meta;
+  const int *order;
+  float *scratch;
+  int *idx_scratch;
+  float *theta;          // [batch][L][T][3], pixels
+  float *loss_out;       // [batch] final loss (may be null)
+  float *loss_hist;      // [batch][steps + 1] (may be null)
+  float *grad_out;       // [batch][L][T][3] (loss-and-gradient mode only)
+  int batch, L, T, steps, loss_kind, mode;  // mode 0 = fit, 1 = loss and gradient
+  float eps, lr0, lr1;
+};
+
+// ---- block reductions ------------------------------------------------------
+
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ float block_sum(float v, float *red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float r = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += red[w];
+  __syncthreads();
+  return r;
+}
+
+__device__ double block_sum_d(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += red[w];
+  __syncthreads();
+  return r;
+}
+
+// ---- SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) ------------------------
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long &st) {
+  unsigned long long z = (st += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ---- initialisation ---------------------------------------------------------
+
+// Eq. 6 rings for layers l0..L-1: radius (l - l0 + 1) dr, angle 2 pi i / T
+// (i = 1..T), weight 1/T.
+__device__ void write_rings(float *th, int L, int T, int l0, double dr) {
+  for (int j = threadIdx.x; j < (L - l0) * T; j += blockDim.x) {
+    const int l = l0 + j / T, i = j % T;
+    const double r = (l - l0 + 1) * dr;
+    const double ang = 2.0 * M_PI * (double)(i + 1) / (double)T;
+    float *t = th + ((size_t)l * T + i) * 3;
+    t[0] = (float)(r * cos(ang));
+    t[1] = (float)(r * sin(ang));
+    t[2] = (float)(1.0 / T);
+  }
+}
+
+__global__ void __launch_bounds__(kFitThreads)
+fit_init_kernel(FitArgs A, int init, unsigned long long seed) {
+  __shared__ double red[kFitWarps];
+  __shared__ int scan[kFitThreads];
+  __shared__ float acc_x[DISK_MAX_TAPS], acc_y[DISK_MAX_TAPS];
+  __shared__ int total;
+  const int b = blockIdx.x;
+  const FitMeta m = A.meta[b];
+  const int K = m.K, h = (K - 1) / 2, KK = K * K, L = A.L, T = A.T;
+  const float *tgt = A.targets + m.tgt_off;
+  float *th = A.theta + (size_t)b * L * T * 3;
+  if (init == 0) return;  // given
+  if (init == 3) {        // random: offsets uniform in [-h/L, h/L], weights 1/T
+    if (threadIdx.x == 0) {
+      unsigned long long st = seed;
+      const double sc = ((K - 1) / 2.0) / L;
+      for (int j = 0; j < L * T; ++j) {
+        const double u0 = (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+        const double u1 = (double)(splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+        th[3 * j] = (float)((2.0 * u0 - 1.0) * sc);
+        th[3 * j + 1] = (float)((2.0 * u1 - 1.0) * sc);
+        th[3 * j + 2] = (float)(1.0 / T);
+      }
+    }
+    return;
+  }
+  // Sparse sampling needs the non-zero pixels in row-major order: an ordered
+  // compaction (per-thread contiguous chunks, exclusive scan of the counts).
+  long long S = 0;
+  if (init == 2) {
+    const int per = (KK + blockDim.x - 1) / blockDim.x;
+    const int j0 = min((int)threadIdx.x * per, KK), j1 = min(j0 + per, KK);
+    int c = 0;
+    for (int j = j0; j < j1; ++j) c += tgt[j] > 0.f;
+    scan[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = 0;
+      for (int t = 0; t < (int)blockDim.x; ++t) { const int v = scan[t]; scan[t] = run; run += v; }
+      total = run;
+    }
+    __syncthreads();
+    int pos = scan[threadIdx.x];
+    int *idx = A.idx_scratch + m.idx_off;
+    for (int j = j0; j < j1; ++j)
+      if (tgt[j] > 0.f) idx[pos++] = j;
+    __syncthreads();
+    S = total;
+  }
+  if (init == 1 || S == 0) {
+    // Eq. 6 step matching the target's per-axis second moment
+    double s0 = 0, sx = 0, sy = 0;
+    for (int j = threadIdx.x; j < KK; j += blockDim.x) {
+      const double t = tgt[j];
+      s0 += t; sx += t * (j % K); sy += t * (j / K);
+    }
+    s0 = block_sum_d(s0, red); sx = block_sum_d(sx, red); sy = block_sum_d(sy, red);
+    double sig = 1.0;
+    if (s0 > 0) {
+      const double mx = sx / s0, my = sy / s0;
+      double var = 0;
+      for (int j = threadIdx.x; j < KK; j += blockDim.x) {
+        const double t = tgt[j], dx = (j % K) - mx, dy = (j / K) - my;
+        var += t * (dx * dx + dy * dy);
+      }
+      var = block_sum_d(var, red);
+      sig = sqrt(var / (2.0 * s0));
+    }
+    write_rings(th, L, T, 0, sig * sqrt(12.0 / ((double)L * (L + 1) * (2 * L + 1))));
+    return;
+  }
+  // Sec. 4.2 sparse sampling: dart throwing over the non-zero pixels with the
+  // Eq. 7 radius, one thread, the same decisions as any exact implementation.
+  const double r0sq = (double)S / ((double)T * M_PI);
+  if (threadIdx.x == 0) {
+    const int *idx = A.idx_scratch + m.idx_off;
+    double r2 = r0sq;
+    int acc = 0, fails = 0;
+    unsigned long long st = seed;
+    long long guard = 0;
+    while (acc < T && guard < (1ll << 26)) {
+      ++guard;
+      const unsigned long long z = splitmix64(st);
+      const int p = idx[z % (unsigned long long)S];
+      const double qx = (double)(p % K - h), qy = (double)(p / K - h);
+      bool ok = true;
+      for (int a = 0; a < acc && ok; ++a) {
+        const double ddx = qx - acc_x[a], ddy = qy - acc_y[a];
+        if (ddx * ddx + ddy * ddy < r2) ok = false;
+      }
+      if (ok) { acc_x[acc] = (float)qx; acc_y[acc] = (float)qy; ++acc; fails = 0; }
+      else if (++fails >= 30 * T) { r2 *= 0.81; fails = 0; if (r2 < 0.25) r2 = 0.0; }
+    }
+    for (; acc < T; ++acc) { acc_x[acc] = 0.f; acc_y[acc] = 0.f; }  // guard tripped
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    th[3 * i] = -acc_x[i];
+    th[3 * i + 1] = -acc_y[i];
+    th[3 * i + 2] = (float)(1.0 / T);
+  }
+  if (L > 1) {
+    double sj = 0;
+    for (int j = 1; j < L; ++j) sj += (double)j * j;
+    write_rings(th, L, T, 1, sqrt(r0sq) / sqrt(2.0 * sj));
+  }
+}
+
+// ---- the persistent fit ------------------------------------------------------
+
+constexpr int kFitMaxTaps = 512;  // L * T limit of the fitter (static shared state)
+
+struct FitShared {
+  float4 taps[kFitMaxTaps];
+  float q[kFitMaxTaps * 3];
+  float mo[kFitMaxTaps * 3];
+  float vo[kFitMaxTaps * 3];
+  float g[kFitMaxTaps * 3];
+  LayerExtent ext[DISK_MAX_LAYERS];
+  float red[kFitWarps];
+};
+
+// taps (pixels) from normalised parameters; layer extents from the taps.
+__device__ void make_taps(FitShared &sh, int L, int T, float s) {
+  for (int j = threadIdx.x; j < L * T; j += blockDim.x)
+    sh.taps[j] = make_float4(sh.q[3 * j] * s, sh.q[3 * j + 1] * s, sh.q[3 * j + 2], 0.f);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int S = 0;
+    for (int l = 0; l < L; ++l) {
+      float mx = 0.f;
+      for (int i = threadIdx.x; i < T; i += 32)
+        mx = fmaxf(mx, fmaxf(fabsf(sh.taps[l * T + i].x), fabsf(sh.taps[l * T + i].y)));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const int H = (int)ceilf(mx) + 1;
+      S += H;
+      if (threadIdx.x == 0) { sh.ext[l].H = H; sh.ext[l].S = S; }
+    }
+  }
+  __syncthreads();
+}
+
+// Forward cascade on planes act[0..L]; returns the loss and leaves dL/dI_L in
+// gL (box of half-width max(S_L, h)).
+__device__ float forward_loss(FitShared &sh, const FitArgs &A, const FitMeta &m, float *const *act,
+                              float *gL, const float *tgt) {
+  const int L = A.L, T = A.T, R = m.R, N = 2 * R + 1, K = m.K, h = (K - 1) / 2;
+  // impulse: zero the footprint layer 1 reads, then the unit impulse at c
+  zero_frame(act[0], R, -1, 2 * sh.ext[0].H);
+  __syncthreads();
+  if (threadIdx.x == 0) act[0][R * N + R] = 1.f;
+  __syncthreads();
+  for (int l = 0; l < L; ++l) {
+    const int S = sh.ext[l].S;
+    canvas_layer(act[l], act[l + 1], R, S, sh.taps + l * T, T, sh.ext[l].H, 1.f);
+    __syncthreads();
+    const int reach = (l + 1 < L) ? S + 2 * sh.ext[l + 1].H : max(S, h);
+    zero_frame(act[l + 1], R, S, reach);
+    __syncthreads();
+  }
+  const int bx = max(sh.ext[L - 1].S, h);
+  const float inv = 1.f / ((float)K * (float)K);
+  const float *KL = act[L];
+  float part = 0.f;
+  const int side = 2 * bx + 1;
+  for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
+    const int v = j / side - bx, u = j % side - bx;
+    const float t = (abs(v) <= h && abs(u) <= h) ? tgt[(v + h) * K + (u + h)] : 0.f;
+    const float d = KL[(R + v) * N + (R + u)] - t;
+    float g;
+    if (A.loss_kind == 0) {
+      part += d * d * inv;
+      g = 2.f * d * inv;
+    } else {
+      const float sq = sqrtf(d * d + A.eps * A.eps);
+      part += (sq - A.eps) * inv;
+      g = d / sq * inv;
+    }
+    gL[(R + v) * N + (R + u)] = g;
+  }
+  return block_sum(part, sh.red);
+}
+
+// Tap gradients of every layer into sh.g (pixel units); ga/gb are the two
+// adjoint planes (ga holds dL/dI_L on entry).
+__device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, float *const *act,
+                         float *ga, float *gb) {
+  const int L = A.L, T = A.T, R = m.R, N = 2 * R + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float *G = ga, *Gn = gb;
+  for (int l = L - 1; l >= 0; --l) {
+    const int S = sh.ext[l].S, side = 2 * S + 1, halo = sh.ext[l].H;
+    const float *prev = act[l];
+    // dL/dw, dL/do of every tap of layer l: one warp per tap, lanes over pixels
+    for (int i = warp; i < T; i += nw) {
+      const float4 t = sh.taps[l * T + i];
+      float fx, fy;
+      const int nx = min(max(split_floor(t.x, fx), -halo), halo - 1);
+      const int ny = min(max(split_floor(t.y, fy), -halo), halo - 1);
+      float gw = 0.f, gdx = 0.f, gdy = 0.f;
+      for (int v = -S; v <= S; ++v) {
+        const float *grow = G + (R + v) * N + R;
+        const float *prow = prev + (R + v + ny) * N + R + nx;
+        for (int u = -S + lane; u <= S; u += 32) {
+          const float g = grow[u];
+          const float *q = prow + u;
+          const float a = q[0], bq = q[1], c = q[N], d = q[N + 1];
+          const float top = a + fx * (bq - a), bot = c + fx * (d - c);
+          gw += g * (top + fy * (bot - top));
+          gdx += g * ((1.f - fy) * (bq - a) + fy * (d - c));
+          gdy += g * (bot - top);
+        }
+      }
+      gw = warp_sum(gw); gdx = warp_sum(gdx); gdy = warp_sum(gdy);
+      if (lane == 0) {
+        float *gg = sh.g + ((size_t)l * T + i) * 3;
+        gg[0] = gdx * t.z; gg[1] = gdy * t.z; gg[2] = gw;
+      }
+    }
+    (void)side;
+    if (l > 0) {
+      // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
+      canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.taps + l * T, T, halo, -1.f);
+    }
+    __syncthreads();
+    float *t = G; G = Gn; Gn = t;
+  }
+}
+
+__global__ void __launch_bounds__(kFitThreads) fit_kernel(FitArgs A) {
+  __shared__ FitShared sh;
+  const int b = A.order[blockIdx.x];
+  const FitMeta m = A.meta[b];
+  const int L = A.L, T = A.T, P = L * T * 3, N = 2 * m.R + 1;
+  const size_t plane = (size_t)N * N;
+  float *base = A.scratch + m.canvas_off;
+  float *act[DISK_MAX_LAYERS + 1];
+  for (int l = 0; l <= L; ++l) act[l] = base + l * plane;
+  float *ga = base + (L + 1) * plane, *gb = base + (L + 2) * plane;
+  const float *tgt = A.targets + m.tgt_off;
+  float *th = A.theta + (size_t)b * P;
+  const float s = m.s;
+  for (int j = threadIdx.x; j < P; j += blockDim.x) {
+    const float v = th[j];
+    sh.q[j] = (j % 3 == 2) ? v : fminf(fmaxf(v / s, -1.f), 1.f);
+    sh.mo[j] = 0.f;
+    sh.vo[j] = 0.f;
+  }
+  __syncthreads();
+  const float b1 = 0.9f, b2 = 0.999f, aeps = 1e-8f;
+  float b1t = 1.f, b2t = 1.f;
+  for (int step = 0; step < A.steps || (A.mode == 1 && step == 0); ++step) {
+    make_taps(sh, L, T, s);
+    const float loss = forward_loss(sh, A, m, act, ga, tgt);
+    __syncthreads();
+    backward(sh, A, m, act, ga, gb);
+    __syncthreads();
+    if (A.mode == 1) {
+      for (int j = threadIdx.x; j < P; j += blockDim.x) A.grad_out[(size_t)b * P + j] = sh.g[j];
+      if (threadIdx.x == 0 && A.loss_out) A.loss_out[b] = loss;
+      return;
+    }
+    if (threadIdx.x == 0 && A.loss_hist) A.loss_hist[(size_t)b * (A.steps + 1) + step] = loss;
+    const float lr = A.steps > 1 ? A.lr0 + (A.lr1 - A.lr0) * (float)step / (float)(A.steps - 1) : A.lr0;
+    b1t *= b1;
+    b2t *= b2;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+      const float gj = (j % 3 == 2) ? sh.g[j] : sh.g[j] * s;
+      const float mj = b1 * sh.mo[j] + (1.f - b1) * gj;
+      const float vj = b2 * sh.vo[j] + (1.f - b2) * gj * gj;
+      sh.mo[j] = mj;
+      sh.vo[j] = vj;
+      const float mh = mj / (1.f - b1t), vh = vj / (1.f - b2t);
+      float qn = sh.q[j] - lr * mh / (sqrtf(vh) + aeps);
+      if (j % 3 != 2) qn = fminf(fmaxf(qn, -1.f), 1.f);
+      sh.q[j] = qn;
+    }
+    __syncthreads();
+  }
+  // final loss at the fitted parameters
+  make_taps(sh, L, T, s);
+  const float loss = forward_loss(sh, A, m, act, ga, tgt);
+  if (threadIdx.x == 0) {
+    if (A.loss_out) A.loss_out[b] = loss;
+    if (A.loss_hist) A.loss_hist[(size_t)b * (A.steps + 1) + A.steps] = loss;
+  }
+  for (int j = threadIdx.x; j < P; j += blockDim.x)
+    th[j] = (j % 3 == 2) ? sh.q[j] : sh.q[j] * s;
+}
+
+// ---- host side -----------------------------------------------------------------
+
+constexpr int kPlanChunk = 512;  // 512 * (40 + 4) bytes: inside the parameter limit
+
+struct PlanChunk {
+  int first, count;
+  FitMeta meta[kPlanChunk];
+  int order[kPlanChunk];
+};
+
+__global__ void plan_upload_kernel(const __grid_constant__ PlanChunk c, FitMeta *meta, int *order) {
+  for (int j = threadIdx.x; j < c.count; j += blockDim.x) {
+    meta[c.first + j] = c.meta[j];
+    order[c.first + j] = c.order[j];
+  }
+}
+
+struct FitPlan {
+  std::vector<FitMeta> meta;
+  std::vector<int> order;
+  size_t scratch_floats = 0, idx_ints = 0, tgt_floats = 0;
+};
+
+int plan_fit(const int *sizes, int batch, int L, FitPlan &plan) {
+  plan.meta.resize(batch);
+  long long toff = 0, coff = 0, ioff = 0;
+  for (int b = 0; b < batch; ++b) {
+    const int K = sizes[b];
+    if (K < 1 || K > 257 || (K & 1) == 0)
+      return fail(DISK_ERR_INVALID_ARG, "target sizes must be odd and in [1, 257]");
+    FitMeta &m = plan.meta[b];
+    m.K = K;
+    const int h = (K - 1) / 2;
+    m.s = (float)std::max(1, h);
+    const int Hmax = (int)std::ceil(m.s) + 1;
+    // every read of the cascade stays within (L + 1) * Hmax of the centre
+    m.R = std::max(h, (L + 1) * Hmax) + 1;
+    m.tgt_off = toff;
+    m.canvas_off = coff;
+    m.idx_off = ioff;
+    toff += (long long)K * K;
+    coff += (long long)(L + 3) * (2 * m.R + 1) * (2 * m.R + 1);
+    ioff += (long long)K * K;
+  }
+  plan.order.resize(batch);
+  std::iota(plan.order.begin(), plan.order.end(), 0);
+  std::stable_sort(plan.order.begin(), plan.order.end(),
+                   [&](int a, int c) { return plan.meta[a].R > plan.meta[c].R; });
+  plan.scratch_floats = coff;
+  plan.idx_ints = ioff;
+  plan.tgt_floats = toff;
+  return DISK_OK;
+}
+
+int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, int steps,
+            float lr0, float lr1, int init, int loss, float eps, unsigned long long seed,
+            float *d_theta, float *d_loss, float *d_hist, float *d_grad, int mode,
+            cudaStream_t s) {
+  if (!d_targets || !sizes || !d_theta) return fail(DISK_ERR_INVALID_ARG, "null pointer");
+  if (batch < 1 || L < 1 || L > DISK_MAX_LAYERS || T < 1 || T > DISK_MAX_TAPS)
+    return fail(DISK_ERR_INVALID_ARG, "batch >= 1, L in [1, 16], T in [1, 64] required");
+  if (L * T > kFitMaxTaps) return fail(DISK_ERR_UNSUPPORTED, "the fitter supports L * T <= 512");
+  if (steps < 0 || steps > 1000000) return fail(DISK_ERR_INVALID_ARG, "steps out of range");
+  if (init < 0 || init > 3 || (loss != 0 && loss != 1))
+    return fail(DISK_ERR_INVALID_ARG, "bad init or loss kind");
+  if (loss == 1 && !(eps > 0.f)) return fail(DISK_ERR_INVALID_ARG, "Charbonnier needs eps > 0");
+  if (!std::isfinite(lr0) || !std::isfinite(lr1)) return fail(DISK_ERR_INVALID_ARG, "bad lr");
+  FitPlan plan;
+  int rc = plan_fit(sizes, batch, L, plan);
+  if (rc) return rc;
+  const size_t meta_bytes = plan.meta.size() * sizeof(FitMeta);
+  const size_t order_bytes = plan.order.size() * sizeof(int);
+  const size_t head = ((meta_bytes + order_bytes + 255) / 256) * 256;
+  const size_t bytes = head + plan.scratch_floats * sizeof(float) + plan.idx_ints * sizeof(int);
+  char *buf = nullptr;
+  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, s), "cudaMallocAsync(fit scratch)");
+  // The plan rides in kernel parameters (no host staging buffer, no sync), so
+  // the whole call can be captured in a CUDA graph.
+  cudaError_t e = cudaSuccess;
+  for (int first = 0; first < batch && e == cudaSuccess; first += kPlanChunk) {
+    static thread_local PlanChunk chunk;
+    chunk.first = first;
+    chunk.count = std::min(kPlanChunk, batch - first);
+    for (int j = 0; j < chunk.count; ++j) {
+      chunk.meta[j] = plan.meta[first + j];
+      chunk.order[j] = plan.order[first + j];
+    }
+    plan_upload_kernel<<<1, 256, 0, s>>>(chunk, reinterpret_cast<FitMeta *>(buf),
+                                         reinterpret_cast<int *>(buf + meta_bytes));
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    cudaFreeAsync(buf, s);
+    return cuda_fail(e, "upload fit plan");
+  }
+  FitArgs A;
+  A.targets = d_targets;
+  A.meta = reinterpret_cast<const FitMeta *>(buf);
+  A.order = reinterpret_cast<const int *>(buf + meta_bytes);
+  A.scratch = reinterpret_cast<float *>(buf + head);
+  A.idx_scratch = reinterpret_cast<int *>(buf + head + plan.scratch_floats * sizeof(float));
+  A.theta = d_theta;
+  A.loss_out = d_loss;
+  A.loss_hist = d_hist;
+  A.grad_out = d_grad;
+  A.batch = batch; A.L = L; A.T = T; A.steps = steps; A.loss_kind = loss; A.mode = mode;
+  A.eps = eps; A.lr0 = lr0; A.lr1 = lr1;
+  if (mode == 0 && init != 0) fit_init_kernel<<<batch, kFitThreads, 0, s>>>(A, init, seed);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    fit_kernel<<<batch, kFitThreads, 0, s>>>(A);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launch fit kernels");
+  return DISK_OK;
+}
+
+}  // namespace
+}  // namespace disk
+
+using namespace disk;
+
+extern "C" int disk_fit(const float *d_targets, const int *sizes, int batch, int L, int T,
+                        int steps, float lr0, float lr1, int init, int loss, float eps,
+                        uint64_t seed, float *d_theta_io, float *d_final_loss,
+                        float *d_loss_hist, void *stream) {
+  return run_fit(d_targets, sizes, batch, L, T, steps, lr0, lr1, init, loss, eps, seed,
+                 d_theta_io, d_final_loss, d_loss_hist, nullptr, 0,
+                 static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int disk_fit_loss_grad(const float *d_targets, const int *sizes, int batch, int L,
+                                  int T, int loss, float eps, const float *d_theta,
+                                  float *d_loss, float *d_grad, void *stream) {
+  if (!d_grad || !d_loss) return fail(DISK_ERR_INVALID_ARG, "null output");
+  return run_fit(d_targets, sizes, batch, L, T, 0, 0.f, 0.f, 0, loss, eps, 0,
+                 const_cast<float *>(d_theta), d_loss, nullptr, d_grad, 1,
+                 static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,57 @@
+// Internal declarations shared by the translation units of libdisk.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "disk.h"
+
+// Immutable basis of complexes (Sec. 4.3, Eq. 8) with its device copy.
+struct disk_basis {
+  int dims = 1;
+  int n_nodes[2] = {1, 1};
+  int L = 0, T = 0, B = 0;
+  std::vector<float> node_vals;  // n_nodes[0] (+ n_nodes[1]) values
+  std::vector<float> theta;      // [B][L][T][3] = (dx, dy, w), pixels
+  std::vector<float> reach;      // [L]: max over nodes, taps of max(|dx|,|dy|)
+  int device = 0;
+  float4 *d_taps = nullptr;      // [L][B][T] = (dx, dy, w, 0)
+};
+
+namespace disk {
+
+// Records a detail message for disk_last_error_message() and returns code.
+int fail(int code, const std::string &msg);
+// Maps a CUDA error to DISK_ERR_OOM / DISK_ERR_CUDA with a detail message.
+int cuda_fail(cudaError_t e, const char *what);
+
+inline int halo_of(float reach) {
+  // Offsets with |o| <= reach touch pixels within ceil(reach) + 1 of the
+  // output pixel (the +1 is the bilinear footprint).
+  return static_cast<int>(__builtin_ceilf(reach)) + 1;
+}
+
+// Kernel-space axis as the kernels see it: node values and inverse spacings.
+struct AxisNodes {
+  int n;
+  float v[DISK_MAX_NODES_AXIS];
+  float inv[DISK_MAX_NODES_AXIS];
+};
+
+void make_axes(int dims, const int *n_nodes, const float *node_vals, AxisNodes ax[2]);
+
+int validate_image_args(const void *d_in, size_t in_pitch, const void *d_out,
+                        size_t out_pitch, int H, int W, int C, int dtype,
+                        const float *d_maps);
+int validate_nodes(int dims, const int *n_nodes, const float *node_vals);
+
+}  // namespace disk
+
+#define DISK_TRY_CUDA(expr, what)                   \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return disk::cuda_fail(e_, what); \
+  } while (0)

@@ -1,0 +1,275 @@
+"""Thin Python binding of libdisk.so (the C ABI in include/disk.h).
+
+Argument marshalling only: torch tensors are checked (device, dtype, layout)
+and their device pointers, pitches and the current stream are handed to the
+C entry points of the same names.  Every step of the computation runs in the
+library's CUDA kernels.  There is no fallback: if libdisk.so is missing or
+fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdisk.so")
+
+DISK_OK = 0
+F32, F16 = 0, 1
+LOSS_MSE, LOSS_CHARB = 0, 1
+INIT_GIVEN, INIT_IR, INIT_SS, INIT_RAND = 0, 1, 2, 3
+
+_vp = ctypes.c_void_p
+_ip = ctypes.POINTER(ctypes.c_int)
+_fp = ctypes.POINTER(ctypes.c_float)
+_sz = ctypes.c_size_t
+_i = ctypes.c_int
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DiskError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} failed: {code} ({msg})")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libdisk.so.  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"libdisk.so not found at {LIB_PATH}: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        l = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "disk_version": (_i, []),
+            "disk_error_string": (ctypes.c_char_p, [_i]),
+            "disk_last_error_message": (ctypes.c_char_p, []),
+            "disk_basis_from_arrays": (_i, [_i, _ip, _fp, _i, _i, _fp, ctypes.POINTER(_vp)]),
+            "disk_basis_load": (_i, [ctypes.c_char_p, ctypes.POINTER(_vp)]),
+            "disk_basis_save": (_i, [_vp, ctypes.c_char_p]),
+            "disk_basis_info": (_i, [_vp, _ip, _ip, _ip, _ip]),
+            "disk_basis_free": (None, [_vp]),
+            "disk_sv_filter": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
+            "disk_dense_sv": (_i, [_i, _ip, _fp, _vp, _i, _vp, _sz, _vp, _sz, _i, _i, _i, _i,
+                                   _vp, _vp]),
+            "disk_synth_kernel": (_i, [_vp, _i, _i, _i, _i, ctypes.c_float, _vp, _vp]),
+            "disk_fit": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, ctypes.c_float, _i, _i,
+                              ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
+            "disk_fit_loss_grad": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _vp,
+                                        _vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(l, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = l
+        return l
+
+
+def exported_symbols() -> list[str]:
+    return [n for n in dir(lib()) if n.startswith("disk_")]
+
+
+def _check(fn: str, rc: int):
+    if rc != DISK_OK:
+        msg = lib().disk_last_error_message().decode(errors="replace")
+        raise DiskError(fn, rc, f"{lib().disk_error_string(rc).decode()}: {msg}")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float16:
+        return F16
+    raise TypeError(f"image dtype must be float32 or float16, got {t.dtype}")
+
+
+def _image_args(t):
+    """(pointer, pitch in bytes, H, W, C) of an H x W x C image whose pixels
+    are contiguous within a row."""
+    if t.dim() != 3 or not t.is_cuda:
+        raise ValueError("image must be a CUDA tensor of shape [H, W, C]")
+    H, W, C = t.shape
+    if t.stride(2) != 1 or t.stride(1) != C:
+        raise ValueError("image rows must be contiguous [W][C]")
+    return t.data_ptr(), t.stride(0) * t.element_size(), H, W, C
+
+
+def _int_arr(v):
+    a = (ctypes.c_int * len(v))(*[int(x) for x in v])
+    return a
+
+
+def _float_arr(v):
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float32).ravel())
+    return (ctypes.c_float * len(v))(*v.tolist()), v
+
+
+class Basis:
+    """A disk_basis handle (Sec. 4.3 Eq. 8): node values per kernel-space axis
+    and theta [B][L][T][3] (dx, dy, w in pixels)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        dims, nn, L, T = _i(), (ctypes.c_int * 2)(), _i(), _i()
+        _check("disk_basis_info", lib().disk_basis_info(self._h, ctypes.byref(dims), nn,
+                                                        ctypes.byref(L), ctypes.byref(T)))
+        self.dims, self.n_nodes, self.L, self.T = dims.value, [nn[0], nn[1]][:dims.value], L.value, T.value
+
+    @classmethod
+    def from_arrays(cls, node_vals, theta) -> "Basis":
+        """node_vals: one increasing sequence per axis (1 or 2 axes)."""
+        if np.ndim(node_vals[0]) == 0:
+            node_vals = [node_vals]
+        n_nodes = [len(v) for v in node_vals]
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float32))
+        B = int(np.prod(n_nodes))
+        if th.ndim != 4 or th.shape[0] != B or th.shape[3] != 3:
+            raise ValueError(f"theta must be [B={B}][L][T][3], got {th.shape}")
+        nv, _ = _float_arr(np.concatenate([np.asarray(v, np.float32) for v in node_vals]))
+        h = _vp()
+        _check("disk_basis_from_arrays", lib().disk_basis_from_arrays(
+            len(n_nodes), _int_arr(n_nodes), nv, th.shape[1], th.shape[2],
+            th.ctypes.data_as(_fp), ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def load(cls, path: str) -> "Basis":
+        h = _vp()
+        _check("disk_basis_load", lib().disk_basis_load(os.fsencode(path), ctypes.byref(h)))
+        return cls(h)
+
+    def save(self, path: str):
+        _check("disk_basis_save", lib().disk_basis_save(self._h, os.fsencode(path)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().disk_basis_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sv_filter(basis: Basis, img, maps, out=None, stream=None):
+    """Spatially varying DISK filter (Eq. 9 + Eq. 3) of an [H, W, C] CUDA
+    image (float32 or float16) with [dims, H, W] float32 maps."""
+    import torch
+    ip, ipitch, H, W, C = _image_args(img)
+    if out is None:
+        out = torch.empty_like(img, memory_format=torch.contiguous_format)
+    op, opitch, *_ = _image_args(out)
+    if out.dtype != img.dtype or tuple(out.shape) != tuple(img.shape):
+        raise ValueError("out must match img in shape and dtype")
+    if maps.dtype != torch.float32 or not maps.is_cuda or not maps.is_contiguous():
+        raise ValueError("maps must be a contiguous float32 CUDA tensor [dims, H, W]")
+    if maps.numel() != basis.dims * H * W:
+        raise ValueError("maps must hold dims * H * W values")
+    _check("disk_sv_filter", lib().disk_sv_filter(
+        basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
+        _vp(maps.data_ptr()), _stream(stream)))
+    return out
+
+
+def dense_sv(node_vals, lut, img, maps, out=None, stream=None):
+    """Dense spatially varying convolution (Eq. 1 per pixel) with node kernels
+    lut [B, Kd, Kd] (float32, CUDA) blended by the Eq. 9 weights."""
+    import torch
+    if np.ndim(node_vals[0]) == 0:
+        node_vals = [node_vals]
+    n_nodes = [len(v) for v in node_vals]
+    nv, _ = _float_arr(np.concatenate([np.asarray(v, np.float32) for v in node_vals]))
+    ip, ipitch, H, W, C = _image_args(img)
+    if out is None:
+        out = torch.empty_like(img, memory_format=torch.contiguous_format)
+    op, opitch, *_ = _image_args(out)
+    if lut.dtype != torch.float32 or not lut.is_cuda or not lut.is_contiguous() or lut.dim() != 3:
+        raise ValueError("lut must be a contiguous float32 CUDA tensor [B, Kd, Kd]")
+    _check("disk_dense_sv", lib().disk_dense_sv(
+        len(n_nodes), _int_arr(n_nodes), nv, _vp(lut.data_ptr()), lut.shape[-1],
+        _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
+        _vp(maps.data_ptr()), _stream(stream)))
+    return out
+
+
+def synth_kernel(theta, K: int, max_reach: float | None = None, out=None, stream=None):
+    """Impulse responses (Eq. 10) of complexes theta [batch, L, T, 3] (float32
+    CUDA, pixels), cropped to K x K."""
+    import torch
+    if theta.dim() == 3:
+        theta = theta[None]
+    if theta.dtype != torch.float32 or not theta.is_cuda or not theta.is_contiguous():
+        raise ValueError("theta must be a contiguous float32 CUDA tensor [batch, L, T, 3]")
+    batch, L, T, _ = theta.shape
+    if max_reach is None:
+        max_reach = float(theta[..., :2].abs().max().item()) if theta.numel() else 0.0
+    if out is None:
+        out = torch.empty((batch, K, K), device=theta.device, dtype=torch.float32)
+    _check("disk_synth_kernel", lib().disk_synth_kernel(
+        _vp(theta.data_ptr()), batch, L, T, K, float(max_reach), _vp(out.data_ptr()),
+        _stream(stream)))
+    return out
+
+
+def pack_targets(targets, device="cuda"):
+    """Packs square odd-sized targets back to back: (device tensor, sizes)."""
+    import torch
+    sizes = [int(t.shape[0]) for t in targets]
+    flat = np.concatenate([np.asarray(t, np.float32).ravel() for t in targets])
+    return torch.from_numpy(flat).to(device), sizes
+
+
+def fit(packed, sizes, L: int, T: int, steps: int, lr0: float = 1e-3, lr1: float = 1e-4,
+        init: int = INIT_IR, loss: int = LOSS_MSE, eps: float = 0.0, seed: int = 0,
+        theta=None, loss_hist: bool = False, stream=None):
+    """Batched fit (Eq. 4) of complexes [batch, L, T, 3] (pixels) to packed
+    targets.  Returns (theta, final loss [batch], history [batch, steps+1] or
+    None)."""
+    import torch
+    batch = len(sizes)
+    dev = packed.device
+    if theta is None:
+        theta = torch.zeros((batch, L, T, 3), device=dev, dtype=torch.float32)
+    final = torch.empty(batch, device=dev, dtype=torch.float32)
+    hist = torch.empty((batch, steps + 1), device=dev, dtype=torch.float32) if loss_hist else None
+    _check("disk_fit", lib().disk_fit(
+        _vp(packed.data_ptr()), _int_arr(sizes), batch, L, T, steps, lr0, lr1, init, loss,
+        eps, seed, _vp(theta.data_ptr()), _vp(final.data_ptr()),
+        _vp(hist.data_ptr()) if hist is not None else None, _stream(stream)))
+    return theta, final, hist
+
+
+def fit_loss_grad(packed, sizes, theta, loss: int = LOSS_MSE, eps: float = 0.0, stream=None):
+    """Fit objective and its gradient at theta [batch, L, T, 3]."""
+    import torch
+    batch, L, T, _ = theta.shape
+    l = torch.empty(batch, device=theta.device, dtype=torch.float32)
+    g = torch.empty_like(theta)
+    _check("disk_fit_loss_grad", lib().disk_fit_loss_grad(
+        _vp(packed.data_ptr()), _int_arr(sizes), batch, L, T, loss, eps,
+        _vp(theta.data_ptr()), _vp(l.data_ptr()), _vp(g.data_ptr()), _stream(stream)))
+    return l, g

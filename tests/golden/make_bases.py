@@ -1,0 +1,92 @@
+"""Fits the bases of the two full-size filtering workloads with the FP64
+oracle's fitter and writes them as basis files (calls only ``oracle/``).
+
+Offline stage of Sec. 4.3: every node's complex is fitted to its own dense
+target with the Eq. 4 objective, Adam and the Sec. 5.1 schedule (1000 steps,
+lr 1e-3 -> 1e-4).  Nodes are fitted in order along the radius axis, each
+warm-started from its neighbour with offsets scaled by the ratio of target
+half-widths, so that tap i means the same tap across nodes and blending them
+(Eq. 9) is meaningful; the first node of each chain starts from the Eq. 6
+radial initialisation.
+
+  bases/disk16_L4T16.dkb    16 disks, radius 1..32 px, L=4, T=16 (1-D)
+  bases/ellipse8x8_L4T24.dkb  8 x 8 ellipses, radius 2..40 px x u in [0,1]
+                            (anisotropy 1+3u, rotation pi u), L=4, T=24 (2-D)
+
+Usage: python tests/golden/make_bases.py [--steps N]
+"""
+import json
+import math
+import multiprocessing as mp
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+OUT = os.path.join(HERE, "bases")
+
+
+def _chain(args):
+    kind, radii, u, L, T, steps = args
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import oracle
+    from paper_2512_04556_gb300 import workloads as wl
+    thetas, losses, prev = [], [], None
+    for r in radii:
+        tgt = wl.disk(r) if kind == "disk" else wl.ellipse(*wl.ellipse_params(r, u))
+        K = tgt.shape[0]
+        hw = max(1.0, (K - 1) / 2)
+        if prev is None:
+            th, hist = oracle.fit(tgt, L, T, steps, init=oracle.INIT_IR)
+        else:
+            th0 = prev[0].copy()
+            th0[..., :2] *= hw / prev[1]
+            th0[..., :2] = np.clip(th0[..., :2], -hw, hw)
+            th, hist = oracle.fit(tgt, L, T, steps, init=oracle.INIT_GIVEN, theta0=th0)
+        rel = hist[-1] * K * K / float((tgt ** 2).sum())
+        thetas.append(th)
+        losses.append(dict(radius=float(r), u=u, K=K, mse=float(hist[-1]), rel_mse=float(rel),
+                           mse0=float(hist[0])))
+        prev = (th, hw)
+    return kind, u, thetas, losses
+
+
+def main(steps=1000):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import basis_io
+    from paper_2512_04556_gb300 import workloads as wl
+    os.makedirs(OUT, exist_ok=True)
+    c2, c4 = wl.C2, wl.C4
+    jobs = [("disk", list(c2["nodes"]), 0.0, c2["L"], c2["T"], steps)]
+    jobs += [("ellipse", list(c4["nodes0"]), float(u), c4["L"], c4["T"], steps) for u in c4["nodes1"]]
+    os.environ["OMP_NUM_THREADS"] = "1"
+    t0 = time.time()
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 4)) as pool:
+        res = pool.map(_chain, jobs)
+    report = {"steps": steps, "seconds": time.time() - t0}
+    disk_th = [r for r in res if r[0] == "disk"][0]
+    basis_io.write(os.path.join(OUT, "disk16_L4T16.dkb"), [c2["nodes"]], np.stack(disk_th[2]))
+    report["disk"] = disk_th[3]
+    ell = {r[1]: r for r in res if r[0] == "ellipse"}
+    th = np.zeros((8, 8, c4["L"], c4["T"], 3))
+    losses = []
+    for b, u in enumerate(c4["nodes1"]):
+        for a in range(8):
+            th[a, b] = ell[float(u)][2][a]
+        losses += ell[float(u)][3]
+    basis_io.write(os.path.join(OUT, "ellipse8x8_L4T24.dkb"), [c4["nodes0"], c4["nodes1"]],
+                   th.reshape(64, c4["L"], c4["T"], 3))
+    report["ellipse"] = losses
+    with open(os.path.join(OUT, "fit_report.json"), "w") as f:
+        json.dump(report, f, indent=1)
+    print(f"wrote bases in {report['seconds']:.0f} s")
+
+
+if __name__ == "__main__":
+    n = 1000
+    if "--steps" in sys.argv:
+        n = int(sys.argv[sys.argv.index("--steps") + 1])
+    main(n)
