@@ -1,0 +1,7 @@
+// Instantiations of the spatially varying layer kernel for 2-D bases.
+#include "sv_layer.cuh"
+
+namespace disk {
+DISK_SV_INSTANTIATE(2, kSvParamTaps)
+DISK_SV_INSTANTIATE(2, 0)
+}  // namespace disk
