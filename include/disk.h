@@ -124,6 +124,34 @@ int disk_sv_filter(const disk_basis *basis, const void *d_in, size_t in_pitch,
                    int dtype, const float *d_maps, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * disk_sv_filter without any allocation.  The paper has no counterpart: this
+ * is a deployment variant of disk_sv_filter.
+ *
+ * Some callers cannot allocate device memory at all: a plug-in inside a host
+ * application that owns the whole device-memory budget, a real-time loop that
+ * forbids allocation after start-up so that its latency stays bounded, or
+ * code that runs where the allocator may not be re-entered.  This entry point
+ * computes exactly what disk_sv_filter computes, with the same arguments,
+ * layouts and status codes, but calls no cudaMalloc, cudaFree or other
+ * allocating routine: the intermediate layers live in one fixed array built
+ * into the library (two FP32 RGBA planes, 32 MiB), which every device that
+ * loads the library holds until the process exits.
+ * Limit: H * W <= 1048576 pixels; larger images return DISK_ERR_UNSUPPORTED
+ *   before any work is queued.
+ * First call on a device: it looks up the array's device address on the
+ *   current device (once per device, then cached), so make that first call
+ *   before capturing a stream into a CUDA graph.
+ * Shared state: every call on a device uses the same array.  The array keeps
+ *   the last call's contents; each layer overwrites every pixel it later
+ *   reads, so nothing has to start at zero.  Calls that overlap on the GPU
+ *   (different streams without ordering between them) race on the array and
+ *   give undefined results: order them on one stream or with events. */
+int disk_sv_filter_noalloc(const disk_basis *basis, const void *d_in,
+                           size_t in_pitch, void *d_out, size_t out_pitch, int H,
+                           int W, int C, int dtype, const float *d_maps,
+                           void *stream);
+
+/* ---------------------------------------------------------------------------
  * Dense spatially varying convolution (Sec. 3.1 Eq. 1 per pixel), the
  * reference DISK approximates and its speed baseline:
  *   out[x] = sum_m K_x[m] * I[clamp(x - m)],  K_x = sum_k alpha_k(x) D_k,

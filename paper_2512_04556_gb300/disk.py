@@ -59,6 +59,7 @@ def lib() -> ctypes.CDLL:
             "disk_basis_info": (_i, [_vp, _ip, _ip, _ip, _ip]),
             "disk_basis_free": (None, [_vp]),
             "disk_sv_filter": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
+            "disk_sv_filter_noalloc": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
             "disk_dense_sv": (_i, [_i, _ip, _fp, _vp, _i, _vp, _sz, _vp, _sz, _i, _i, _i, _i,
                                    _vp, _vp]),
             "disk_synth_kernel": (_i, [_vp, _i, _i, _i, _i, ctypes.c_float, _vp, _vp]),
@@ -190,6 +191,24 @@ def sv_filter(basis: Basis, img, maps, out=None, stream=None):
     if maps.numel() != basis.dims * H * W:
         raise ValueError("maps must hold dims * H * W values")
     _check("disk_sv_filter", lib().disk_sv_filter(
+        basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
+        _vp(maps.data_ptr()), _stream(stream)))
+    return out
+
+
+def sv_filter_noalloc(basis: Basis, img, maps, out, stream=None):
+    """disk_sv_filter_noalloc: the same filter for callers that cannot
+    allocate device memory.  ``out`` must be given (nothing is allocated)."""
+    import torch
+    ip, ipitch, H, W, C = _image_args(img)
+    op, opitch, *_ = _image_args(out)
+    if out.dtype != img.dtype or tuple(out.shape) != tuple(img.shape):
+        raise ValueError("out must match img in shape and dtype")
+    if maps.dtype != torch.float32 or not maps.is_cuda or not maps.is_contiguous():
+        raise ValueError("maps must be a contiguous float32 CUDA tensor [dims, H, W]")
+    if maps.numel() != basis.dims * H * W:
+        raise ValueError("maps must hold dims * H * W values")
+    _check("disk_sv_filter_noalloc", lib().disk_sv_filter_noalloc(
         basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
         _vp(maps.data_ptr()), _stream(stream)))
     return out
