@@ -117,8 +117,11 @@ void disk_basis_free(disk_basis *basis);
  *   not overlap.
  * d_maps: float [dims][H][W], dense, raw parameter values.
  * Limits: 1 <= H, W <= 32768; C in {3, 4}.
- * Scratch: 2 * H * W * 16 bytes (L >= 3) or H * W * 16 bytes (L = 2) from
- *   the stream's pool for the intermediate layers, freed on the stream. */
+ * Intermediate layers are stored in the image's precision: FP32 RGBA for
+ *   DISK_F32, FP16 RGBA (round to nearest even) for DISK_F16; arithmetic and
+ *   accumulation are FP32 in both.
+ * Scratch: 2 * H * W * E bytes (L >= 3) or H * W * E bytes (L = 2), E = 16
+ *   (FP32) or 8 (FP16), from the stream's pool, freed on the stream. */
 int disk_sv_filter(const disk_basis *basis, const void *d_in, size_t in_pitch,
                    void *d_out, size_t out_pitch, int H, int W, int C,
                    int dtype, const float *d_maps, void *stream);

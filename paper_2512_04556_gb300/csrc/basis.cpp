@@ -126,7 +126,7 @@ extern "C" int disk_basis_from_arrays(int dims, const int *n_nodes, const float 
         if (r > DISK_MAX_REACH)
           return fail(DISK_ERR_UNSUPPORTED, "tap offset beyond DISK_MAX_REACH");
         b->reach[l] = std::fmax(b->reach[l], r);
-        taps[((size_t)l * b->B + k) * T + i] = make_float4(t[0], t[1], t[2], 0.f);
+        taps[((size_t)l * b->B + k) * T + i] = make_float4(t[0], t[1], t[2], t[2]);
       }
   DISK_TRY_CUDA(cudaGetDevice(&b->device), "cudaGetDevice");
   DISK_TRY_CUDA(cudaMalloc(&b->d_taps, taps.size() * sizeof(float4)), "cudaMalloc(basis)");

@@ -18,7 +18,7 @@ struct disk_basis {
   std::vector<float> theta;      // [B][L][T][3] = (dx, dy, w), pixels
   std::vector<float> reach;      // [L]: max over nodes, taps of max(|dx|,|dy|)
   int device = 0;
-  float4 *d_taps = nullptr;      // [L][B][T] = (dx, dy, w, 0)
+  float4 *d_taps = nullptr;      // [L][B][T] = (dx, dy, w, w)
 };
 
 namespace disk {

@@ -12,16 +12,48 @@ namespace disk {
 
 // Storage kinds of an image operand.
 enum PixKind : int {
-  PIX_RGBA32 = 0,  // library intermediate: float4 per pixel, dense rows
+  PIX_RGBA32 = 0,  // library intermediate for FP32 images: float4 per pixel, dense rows
   PIX_F32 = 1,     // caller image: C floats per pixel
-  PIX_F16 = 2      // caller image: C halves per pixel
+  PIX_F16 = 2,     // caller image: C halves per pixel
+  PIX_RGBA16 = 3   // library intermediate for FP16 images: 4 halves per pixel, dense rows
 };
+
+// Intermediate planes keep the caller's storage precision: FP32 RGBA for
+// FP32 images, FP16 RGBA for FP16 images (arithmetic is FP32 either way).
+__host__ __device__ inline int intermediate_kind(int dtype) {
+  return dtype == DISK_F32 ? PIX_RGBA32 : PIX_RGBA16;
+}
+__host__ __device__ inline size_t kind_bytes(int kind) { return kind == PIX_RGBA32 ? 16 : 8; }
+
+// Four halves <-> two 32-bit words (x holds channels 0,1; y holds 2,3).
+__device__ __forceinline__ uint2 pack_half4(float4 v) {
+  const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+  return make_uint2(*reinterpret_cast<const unsigned *>(&a), *reinterpret_cast<const unsigned *>(&b));
+}
+__device__ __forceinline__ float4 unpack_half4(uint2 u) {
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Raw FP16 RGBA of one pixel of an FP16 source (no rounding: the values are
+// already halves).
+template <int KIND>
+__device__ __forceinline__ uint2 load_raw16(const void *base, long long pitch, int C, int y, int x) {
+  const char *row = static_cast<const char *>(base) + (long long)y * pitch;
+  if (KIND == PIX_RGBA16) return __ldg(reinterpret_cast<const uint2 *>(row) + x);
+  const unsigned short *p = reinterpret_cast<const unsigned short *>(row) + (long long)x * C;
+  const unsigned a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = C == 4 ? __ldg(p + 3) : 0u;
+  return make_uint2(a | (b << 16), c | (d << 16));
+}
 
 template <int KIND>
 __device__ __forceinline__ float4 load_px(const void *base, long long pitch, int C, int y, int x) {
   const char *row = static_cast<const char *>(base) + (long long)y * pitch;
   if (KIND == PIX_RGBA32) {
     return __ldg(reinterpret_cast<const float4 *>(row) + x);
+  } else if (KIND == PIX_RGBA16) {
+    return unpack_half4(__ldg(reinterpret_cast<const uint2 *>(row) + x));
   } else if (KIND == PIX_F32) {
     const float *p = reinterpret_cast<const float *>(row) + (long long)x * C;
     return make_float4(__ldg(p), __ldg(p + 1), __ldg(p + 2), C == 4 ? __ldg(p + 3) : 0.f);
@@ -37,6 +69,8 @@ __device__ __forceinline__ void store_px(void *base, long long pitch, int C, int
   char *row = static_cast<char *>(base) + (long long)y * pitch;
   if (KIND == PIX_RGBA32) {
     reinterpret_cast<float4 *>(row)[x] = v;
+  } else if (KIND == PIX_RGBA16) {
+    reinterpret_cast<uint2 *>(row)[x] = pack_half4(v);
   } else if (KIND == PIX_F32) {
     float *p = reinterpret_cast<float *>(row) + (long long)x * C;
     p[0] = v.x; p[1] = v.y; p[2] = v.z;

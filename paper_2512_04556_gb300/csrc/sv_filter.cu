@@ -1,8 +1,9 @@
 // disk_sv_filter: the spatially varying cascade (Sec. 4.3 Eq. 9 + Sec. 3.2
 // Eq. 3) as one shared-memory-staged launch per layer (kernel in
-// sv_layer.cuh).  Intermediate layers live in FP32 RGBA planes taken from the
-// stream-ordered pool; the first layer reads the caller's image in its
-// storage type and the last writes the caller's output in it.
+// sv_layer.cuh).  Intermediate layers live in RGBA planes of the image's
+// storage precision (FP32 or FP16) taken from the stream-ordered pool; the
+// first layer reads the caller's image and the last writes the caller's
+// output.
 #include "sv_layer.cuh"
 
 namespace disk {
@@ -18,12 +19,14 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
+  const int mid = intermediate_kind(dtype);
+  const size_t mid_bytes = kind_bytes(mid);
   const int L = b->L;
-  float4 *bufs[2] = {nullptr, nullptr};
-  const size_t plane = (size_t)H * W * sizeof(float4);
+  void *bufs[2] = {nullptr, nullptr};
+  const size_t plane = (size_t)H * W * mid_bytes;
   const int nbuf = L >= 3 ? 2 : (L == 2 ? 1 : 0);
   for (int i = 0; i < nbuf; ++i) {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&bufs[i]), plane, s);
+    cudaError_t e = cudaMallocAsync(&bufs[i], plane, s);
     if (e != cudaSuccess) {
       if (i) cudaFreeAsync(bufs[0], s);
       return cuda_fail(e, "cudaMallocAsync(sv_filter scratch)");
@@ -33,12 +36,12 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   for (int l = 0; l < L && rc == DISK_OK; ++l) {
     P.halo = halo_of(b->reach[l]);
     P.region_w = kSvTileW + 2 * P.halo;
-    const int src = l == 0 ? user : PIX_RGBA32;
-    const int dst = l == L - 1 ? user : PIX_RGBA32;
+    const int src = l == 0 ? user : mid;
+    const int dst = l == L - 1 ? user : mid;
     P.src = l == 0 ? d_in : bufs[(l - 1) & 1];
-    P.src_pitch = l == 0 ? (long long)in_pitch : (long long)W * sizeof(float4);
+    P.src_pitch = l == 0 ? (long long)in_pitch : (long long)(W * mid_bytes);
     P.dst = l == L - 1 ? d_out : bufs[l & 1];
-    P.dst_pitch = l == L - 1 ? (long long)out_pitch : (long long)W * sizeof(float4);
+    P.dst_pitch = l == L - 1 ? (long long)out_pitch : (long long)(W * mid_bytes);
     P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
     if (NP > 0) {
       // Tap table of this layer into the parameter block (host copy of the
@@ -46,7 +49,7 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
       for (int k = 0; k < b->B; ++k)
         for (int i = 0; i < b->T; ++i) {
           const float *t = &b->theta[(((size_t)k * L + l) * b->T + i) * 3];
-          P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], 0.f);
+          P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
         }
     }
     rc = b->dims == 1 ? launch_sv_layer<1, NP>(src, dst, C, P, s)
@@ -72,7 +75,7 @@ extern "C" int disk_sv_filter(const disk_basis *b, const void *d_in, size_t in_p
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
   for (int l = 0; l < b->L; ++l) {
     const int h = halo_of(b->reach[l]);
-    const size_t smem = (size_t)(kSvTileW + 2 * h) * (kSvTileH + 2 * h) * sizeof(float4);
+    const size_t smem = (size_t)(kSvTileW + 2 * h) * (kSvTileH + 2 * h) * (dtype == DISK_F32 ? 16 : 8);
     if (smem > (size_t)kSvMaxSmem) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);

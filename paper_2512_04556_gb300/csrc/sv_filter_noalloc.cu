@@ -11,9 +11,9 @@ namespace {
 
 constexpr long long kNoAllocMaxPixels = 1ll << 20;  // H * W limit: 1,048,576 pixels
 
-// Two FP32 RGBA intermediate planes of up to kNoAllocMaxPixels pixels each:
-// 32 MiB that every device which loads the library holds until the process
-// exits.  Every layer overwrites each pixel of its plane before the next
+// Room for two FP32 RGBA intermediate planes of up to kNoAllocMaxPixels
+// pixels each (FP16 images use FP16 planes and half of it): 32 MiB that every
+// device which loads the library holds until the process exits.  Every layer overwrites each pixel of its plane before the next
 // layer reads it, so nothing needs clearing between calls.
 static __device__ __align__(256) float4 g_noalloc_planes[2 * kNoAllocMaxPixels];
 
@@ -46,24 +46,29 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
+  const int mid = intermediate_kind(dtype);
+  const size_t mid_bytes = kind_bytes(mid);
   const int L = b->L;
-  float4 *bufs[2] = {planes, planes + (size_t)H * W};
+  // plane 0 at the start of the array, plane 1 after H * W pixels of the
+  // intermediate kind (both fit: the array holds two FP32 RGBA planes)
+  char *bufs[2] = {reinterpret_cast<char *>(planes),
+                   reinterpret_cast<char *>(planes) + (size_t)H * W * mid_bytes};
   int rc = DISK_OK;
   for (int l = 0; l < L && rc == DISK_OK; ++l) {
     P.halo = halo_of(b->reach[l]);
     P.region_w = kSvTileW + 2 * P.halo;
-    const int src = l == 0 ? user : PIX_RGBA32;
-    const int dst = l == L - 1 ? user : PIX_RGBA32;
+    const int src = l == 0 ? user : mid;
+    const int dst = l == L - 1 ? user : mid;
     P.src = l == 0 ? d_in : bufs[(l - 1) & 1];
-    P.src_pitch = l == 0 ? (long long)in_pitch : (long long)W * sizeof(float4);
+    P.src_pitch = l == 0 ? (long long)in_pitch : (long long)(W * mid_bytes);
     P.dst = l == L - 1 ? d_out : bufs[l & 1];
-    P.dst_pitch = l == L - 1 ? (long long)out_pitch : (long long)W * sizeof(float4);
+    P.dst_pitch = l == L - 1 ? (long long)out_pitch : (long long)(W * mid_bytes);
     P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
     if (NP > 0) {
       for (int k = 0; k < b->B; ++k)
         for (int i = 0; i < b->T; ++i) {
           const float *t = &b->theta[(((size_t)k * L + l) * b->T + i) * 3];
-          P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], 0.f);
+          P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
         }
     }
     rc = b->dims == 1 ? launch_sv_layer<1, NP>(src, dst, C, P, s)
@@ -90,7 +95,7 @@ extern "C" int disk_sv_filter_noalloc(const disk_basis *b, const void *d_in, siz
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
   for (int l = 0; l < b->L; ++l) {
     const int h = halo_of(b->reach[l]);
-    const size_t smem = (size_t)(kSvTileW + 2 * h) * (kSvTileH + 2 * h) * sizeof(float4);
+    const size_t smem = (size_t)(kSvTileW + 2 * h) * (kSvTileH + 2 * h) * (dtype == DISK_F32 ? 16 : 8);
     if (smem > (size_t)kSvMaxSmem) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
   }
   float4 *planes = nullptr;

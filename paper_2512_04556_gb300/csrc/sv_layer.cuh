@@ -2,15 +2,19 @@
 // Eq. 3): the kernel template shared by the 1-D and 2-D translation units.
 //
 // Each CTA owns a 32 x 32 output tile.  It stages the layer's source region
-// (tile + the layer's halo, clamp-to-edge) into shared memory as FP32 RGBA,
-// one 16-byte entry per pixel, so each bilinear corner is one 16-byte shared
-// load and a warp's 32 lanes (consecutive columns) read conflict-free.
+// (tile + the layer's halo, clamp-to-edge) into shared memory in the image's
+// storage precision -- FP32 RGBA (16 B) for FP32 images, FP16 RGBA (8 B) for
+// FP16 images, whose planes are FP16 throughout -- so each bilinear corner is
+// one vector shared load and a warp's 32 lanes (consecutive columns) read
+// consecutive entries.  Arithmetic and accumulation are FP32.
 // Every thread owns four pixels of one column (rows r, r+8, r+16, r+24).
 // When all pixels of a warp sit in the same kernel-space cell -- the common
 // case, parameter maps being smooth -- the node taps of each tap index are
 // fetched once (warp-uniform constant-bank loads) and blended for the four
 // pixels with each pixel's own weights; other warps take the per-pixel path.
 #pragma once
+
+#include <type_traits>
 
 #include "sv_common.cuh"
 
@@ -29,10 +33,10 @@ struct SvLayerParams {
   void *dst;
   long long dst_pitch;
   const float *maps;
-  const float4 *gtaps;  // [B][T] of this layer when NP == 0
+  const float4 *gtaps;  // [B][T] of this layer when NP == 0: (dx, dy, w, w)
   int H, W, C, T, halo, region_w;
   AxisNodes ax[2];
-  float4 taps[NP > 0 ? NP : 1];  // [B][T] of this layer when NP > 0
+  float4 taps[NP > 0 ? NP : 1];  // [B][T] of this layer when NP > 0: (dx, dy, w, w)
 };
 
 template <int NP>
@@ -41,40 +45,92 @@ __device__ __forceinline__ float4 node_tap(const SvLayerParams<NP> &P, int idx) 
   return __ldg(P.gtaps + idx);
 }
 
-// One tap of one pixel: Eq. 9 blend of the node taps with the pixel's
-// weights, then the Eq. 2 bilinear sample from the staged region.
-template <int DIMS, int CH>
-__device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, const float4 &q01,
-                                       const float4 &q11, const Cell &c, const float4 *base,
-                                       int RW, int halo, float4 &acc) {
-  float dx = c.a00 * q00.x + c.a10 * q10.x;
-  float dy = c.a00 * q00.y + c.a10 * q10.y;
-  float w = c.a00 * q00.z + c.a10 * q10.z;
-  if (DIMS == 2) {
-    dx += c.a01 * q01.x + c.a11 * q11.x;
-    dy += c.a01 * q01.y + c.a11 * q11.y;
-    w += c.a01 * q01.z + c.a11 * q11.z;
+// Pixel weights of Eq. 9 broadcast into FP32 pairs for the packed
+// (f32x2) arithmetic of sv_tap; built once per pixel.
+struct CellPairs {
+  float2 a00, a10, a01, a11;
+};
+
+__device__ __forceinline__ CellPairs cell_pairs(const Cell &c) {
+  return {make_float2(c.a00, c.a00), make_float2(c.a10, c.a10), make_float2(c.a01, c.a01),
+          make_float2(c.a11, c.a11)};
+}
+
+// Per-pixel accumulator: (r, g) as a packed pair, b and a scalar.
+struct Acc {
+  float2 rg;
+  float b, a;
+};
+
+__device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
+
+// Weighted corner into the accumulator, from an FP32 or FP16 staged pixel.
+template <int CH>
+__device__ __forceinline__ void add_corner(const float4 &v, const float2 &wb, Acc &acc) {
+  acc.rg = __ffma2_rn(wb, lo2(v), acc.rg);
+  acc.b = fmaf(wb.x, v.z, acc.b);
+  if (CH == 4) acc.a = fmaf(wb.x, v.w, acc.a);
+}
+template <int CH>
+__device__ __forceinline__ void add_corner(const uint2 &u, const float2 &wb, Acc &acc) {
+  acc.rg = __ffma2_rn(wb, __half22float2(*reinterpret_cast<const __half2 *>(&u.x)), acc.rg);
+  if (CH == 4) {
+    const float2 ba = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    acc.b = fmaf(wb.x, ba.x, acc.b);
+    acc.a = fmaf(wb.x, ba.y, acc.a);
+  } else {
+    acc.b = fmaf(wb.x, __low2float(*reinterpret_cast<const __half2 *>(&u.y)), acc.b);
   }
+}
+
+// One tap of one pixel: the Eq. 9 blend of the node taps (dx, dy, w, w) with
+// the pixel's weights, the integer/fraction split of the offset, and the
+// Eq. 2 bilinear sample from the staged region, all in packed FP32 pairs:
+// (dx, dy) and the corner weights travel as pairs, colour as (r, g) + b.
+template <int DIMS, int CH, typename ST>
+__device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, const float4 &q01,
+                                       const float4 &q11, const CellPairs &a, const ST *base,
+                                       int RW, int halo, Acc &acc) {
+  float2 d = __fmul2_rn(a.a00, lo2(q00));
+  float2 w = __fmul2_rn(a.a00, hi2(q00));
+  d = __ffma2_rn(a.a10, lo2(q10), d);
+  w = __ffma2_rn(a.a10, hi2(q10), w);
+  if (DIMS == 2) {
+    d = __ffma2_rn(a.a01, lo2(q01), d);
+    w = __ffma2_rn(a.a01, hi2(q01), w);
+    d = __ffma2_rn(a.a11, lo2(q11), d);
+    w = __ffma2_rn(a.a11, hi2(q11), w);
+  }
+  // integer part n = round-to-nearest(d - 1/2) (= floor(d) except at exact
+  // integers, where bilinear sampling gives the same value either way) and
+  // fraction f = d - n in [0, 1], for both axes at once; see split_offset.
+  const float magic = 12582912.0f;
+  const float2 r = __fadd2_rn(__fadd2_rn(d, make_float2(-0.5f, -0.5f)), make_float2(magic, magic));
+  const float2 f = __ffma2_rn(__fadd2_rn(r, make_float2(-magic, -magic)), make_float2(-1.f, -1.f), d);
   // Convexity of Eq. 9 bounds every blended offset by the layer reach, so
   // nx, ny already lie in [-halo, halo - 1]; the clamp only guarantees that
   // shared memory is never read outside the staged region.
-  float fx, fy;
-  const int nx = min(max(split_offset(dx, fx), -halo), halo - 1);
-  const int ny = min(max(split_offset(dy, fy), -halo), halo - 1);
-  const float4 *q = base + ny * RW + nx;
-  const float4 c00 = q[0], c01 = q[1], c10 = q[RW], c11 = q[RW + 1];
-  const float wy1 = w * fy, wy0 = w - wy1;
-  const float w11 = wy1 * fx, w10 = wy1 - w11, w01 = wy0 * fx, w00 = wy0 - w01;
-  acc.x += w00 * c00.x + w01 * c01.x + w10 * c10.x + w11 * c11.x;
-  acc.y += w00 * c00.y + w01 * c01.y + w10 * c10.y + w11 * c11.y;
-  acc.z += w00 * c00.z + w01 * c01.z + w10 * c10.z + w11 * c11.z;
-  if (CH == 4) acc.w += w00 * c00.w + w01 * c01.w + w10 * c10.w + w11 * c11.w;
+  const int nx = min(max(__float_as_int(r.x) - 0x4B400000, -halo), halo - 1);
+  const int ny = min(max(__float_as_int(r.y) - 0x4B400000, -halo), halo - 1);
+  const ST *q = base + ny * RW + nx;
+  const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y);
+  const float2 wy1 = __fmul2_rn(w, fy), wy0 = __ffma2_rn(wy1, make_float2(-1.f, -1.f), w);
+  const float2 w11 = __fmul2_rn(wy1, fx), w10 = __ffma2_rn(w11, make_float2(-1.f, -1.f), wy1);
+  const float2 w01 = __fmul2_rn(wy0, fx), w00 = __ffma2_rn(w01, make_float2(-1.f, -1.f), wy0);
+  add_corner<CH>(q[0], w00, acc);
+  add_corner<CH>(q[1], w01, acc);
+  add_corner<CH>(q[RW], w10, acc);
+  add_corner<CH>(q[RW + 1], w11, acc);
 }
 
 template <int DIMS, int SRC, int DST, int NP, int CH>
-__global__ void __launch_bounds__(kSvThreads, 2)
+__global__ void __launch_bounds__(kSvThreads, 3)
 sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
-  extern __shared__ float4 sm[];
+  constexpr bool kHalf = SRC == PIX_F16 || SRC == PIX_RGBA16;
+  using ST = typename std::conditional<kHalf, uint2, float4>::type;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  ST *sm = reinterpret_cast<ST *>(sm_raw);
   const int halo = P.halo, RW = P.region_w, RH = kSvTileH + 2 * halo;
   const int tx0 = blockIdx.x * kSvTileW, ty0 = blockIdx.y * kSvTileH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -85,7 +141,10 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     const int gy = min(max(ty0 - halo + ry, 0), P.H - 1);
     for (int rx = lane; rx < RW; rx += 32) {
       const int gx = min(max(tx0 - halo + rx, 0), P.W - 1);
-      sm[ry * RW + rx] = load_px<SRC>(P.src, P.src_pitch, P.C, gy, gx);
+      if constexpr (kHalf)
+        sm[ry * RW + rx] = load_raw16<SRC>(P.src, P.src_pitch, P.C, gy, gx);
+      else
+        sm[ry * RW + rx] = load_px<SRC>(P.src, P.src_pitch, P.C, gy, gx);
     }
   }
   __syncthreads();
@@ -94,39 +153,42 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   const long long HW = (long long)P.H * P.W;
   const int T = P.T;
   Cell c[kSvPix];
-  const float4 *base[kSvPix];
-  float4 acc[kSvPix];
+  CellPairs cp[kSvPix];
+  const ST *base[kSvPix];
+  Acc acc[kSvPix];
   bool same = true;
 #pragma unroll
   for (int j = 0; j < kSvPix; ++j) {
     const int r = warp + kSvWarps * j;
     const int yc = min(ty0 + r, P.H - 1);
     c[j] = make_cell<DIMS>(P.ax, P.maps, HW, (long long)yc * P.W + xc);
+    cp[j] = cell_pairs(c[j]);
     base[j] = sm + (r + halo) * RW + (lane + halo);
-    acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
     same = same && (c[j].n00 == c[0].n00);
   }
   if (__all_sync(0xffffffffu, same)) {
     // one node fetch per tap serves the thread's four pixels
     const int b00 = c[0].n00 * T, b10 = c[0].n10 * T, b01 = c[0].n01 * T, b11 = c[0].n11 * T;
-#pragma unroll 2
+#pragma unroll 1
     for (int i = 0; i < T; ++i) {
       const float4 q00 = node_tap(P, b00 + i), q10 = node_tap(P, b10 + i);
       const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
       const float4 q11 = DIMS == 2 ? node_tap(P, b11 + i) : q10;
 #pragma unroll
-      for (int j = 0; j < kSvPix; ++j) sv_tap<DIMS, CH>(q00, q10, q01, q11, c[j], base[j], RW, halo, acc[j]);
+      for (int j = 0; j < kSvPix; ++j) sv_tap<DIMS, CH, ST>(q00, q10, q01, q11, cp[j], base[j], RW, halo, acc[j]);
     }
   } else {
-#pragma unroll 1
+    // unrolled so the per-pixel arrays stay in registers
+#pragma unroll
     for (int j = 0; j < kSvPix; ++j) {
       const int b00 = c[j].n00 * T, b10 = c[j].n10 * T, b01 = c[j].n01 * T, b11 = c[j].n11 * T;
-#pragma unroll 2
+#pragma unroll 1
       for (int i = 0; i < T; ++i) {
         const float4 q00 = node_tap(P, b00 + i), q10 = node_tap(P, b10 + i);
         const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
         const float4 q11 = DIMS == 2 ? node_tap(P, b11 + i) : q10;
-        sv_tap<DIMS, CH>(q00, q10, q01, q11, c[j], base[j], RW, halo, acc[j]);
+        sv_tap<DIMS, CH, ST>(q00, q10, q01, q11, cp[j], base[j], RW, halo, acc[j]);
       }
     }
   }
@@ -134,7 +196,9 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
 #pragma unroll
     for (int j = 0; j < kSvPix; ++j) {
       const int y = ty0 + warp + kSvWarps * j;
-      if (y < P.H) store_px<DST>(P.dst, P.dst_pitch, P.C, y, x, acc[j]);
+      if (y < P.H)
+        store_px<DST>(P.dst, P.dst_pitch, P.C, y, x,
+                      make_float4(acc[j].rg.x, acc[j].rg.y, acc[j].b, acc[j].a));
     }
   }
 }
@@ -142,7 +206,8 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
 template <int DIMS, int SRC, int DST, int NP, int CH>
 int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
   auto k = sv_layer_kernel<DIMS, SRC, DST, NP, CH>;
-  const size_t smem = (size_t)P.region_w * (kSvTileH + 2 * P.halo) * sizeof(float4);
+  const size_t px_bytes = (SRC == PIX_F16 || SRC == PIX_RGBA16) ? 8 : 16;
+  const size_t smem = (size_t)P.region_w * (kSvTileH + 2 * P.halo) * px_bytes;
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
   int dev = 0;
   cudaGetDevice(&dev);
@@ -161,32 +226,24 @@ int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
 template <int DIMS, int NP>
 int launch_sv_layer(int src, int dst, int C, const SvLayerParams<NP> &P, cudaStream_t s);
 
-#define DISK_SV_INSTANTIATE(DIMS, NP)                                                         \
+#define DISK_SV_CASE(DIMS, NP, S, D)                                                        \
+  if (src == S && dst == D)                                                                 \
+    return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4>(P, s) : launch_sv_layer_t<DIMS, S, D, NP, 3>(P, s);
+
+// FP32 images: FP32 planes; FP16 images: FP16 planes (see intermediate_kind).
+#define DISK_SV_INSTANTIATE(DIMS, NP)                                                       \
   template <>                                                                               \
   int launch_sv_layer<DIMS, NP>(int src, int dst, int C, const SvLayerParams<NP> &P,          \
                                 cudaStream_t s) {                                           \
     const bool c4 = C == 4;                                                                 \
-    if (src == PIX_F32 && dst == PIX_RGBA32)                                                \
-      return c4 ? launch_sv_layer_t<DIMS, PIX_F32, PIX_RGBA32, NP, 4>(P, s)                 \
-                : launch_sv_layer_t<DIMS, PIX_F32, PIX_RGBA32, NP, 3>(P, s);                \
-    if (src == PIX_F16 && dst == PIX_RGBA32)                                                \
-      return c4 ? launch_sv_layer_t<DIMS, PIX_F16, PIX_RGBA32, NP, 4>(P, s)                 \
-                : launch_sv_layer_t<DIMS, PIX_F16, PIX_RGBA32, NP, 3>(P, s);                \
-    if (src == PIX_RGBA32 && dst == PIX_RGBA32)                                             \
-      return c4 ? launch_sv_layer_t<DIMS, PIX_RGBA32, PIX_RGBA32, NP, 4>(P, s)              \
-                : launch_sv_layer_t<DIMS, PIX_RGBA32, PIX_RGBA32, NP, 3>(P, s);             \
-    if (src == PIX_RGBA32 && dst == PIX_F32)                                                \
-      return c4 ? launch_sv_layer_t<DIMS, PIX_RGBA32, PIX_F32, NP, 4>(P, s)                 \
-                : launch_sv_layer_t<DIMS, PIX_RGBA32, PIX_F32, NP, 3>(P, s);                \
-    if (src == PIX_RGBA32 && dst == PIX_F16)                                                \
-      return c4 ? launch_sv_layer_t<DIMS, PIX_RGBA32, PIX_F16, NP, 4>(P, s)                 \
-                : launch_sv_layer_t<DIMS, PIX_RGBA32, PIX_F16, NP, 3>(P, s);                \
-    if (src == PIX_F32 && dst == PIX_F32)                                                   \
-      return c4 ? launch_sv_layer_t<DIMS, PIX_F32, PIX_F32, NP, 4>(P, s)                    \
-                : launch_sv_layer_t<DIMS, PIX_F32, PIX_F32, NP, 3>(P, s);                   \
-    if (src == PIX_F16 && dst == PIX_F16)                                                   \
-      return c4 ? launch_sv_layer_t<DIMS, PIX_F16, PIX_F16, NP, 4>(P, s)                    \
-                : launch_sv_layer_t<DIMS, PIX_F16, PIX_F16, NP, 3>(P, s);                   \
+    DISK_SV_CASE(DIMS, NP, PIX_F32, PIX_RGBA32)                                             \
+    DISK_SV_CASE(DIMS, NP, PIX_RGBA32, PIX_RGBA32)                                          \
+    DISK_SV_CASE(DIMS, NP, PIX_RGBA32, PIX_F32)                                             \
+    DISK_SV_CASE(DIMS, NP, PIX_F32, PIX_F32)                                                \
+    DISK_SV_CASE(DIMS, NP, PIX_F16, PIX_RGBA16)                                             \
+    DISK_SV_CASE(DIMS, NP, PIX_RGBA16, PIX_RGBA16)                                          \
+    DISK_SV_CASE(DIMS, NP, PIX_RGBA16, PIX_F16)                                             \
+    DISK_SV_CASE(DIMS, NP, PIX_F16, PIX_F16)                                                \
     return fail(DISK_ERR_INVALID_ARG, "unsupported layer storage combination");            \
   }
 
