@@ -214,6 +214,24 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
                   "h2d_bytes_per_step": int(h_img.numel() * 2 + h_maps.numel() * 4),
                   "d2h_bytes_per_step": int(h_out.numel() * 2), "ms_per_step": e2e_ms}
 
+    # image-gradient backward on the same frame (transpose of the cascade)
+    g_out = torch.empty_like(d_img).uniform_(-1, 1)
+    g_in = torch.empty((H, W, 3), device="cuda", dtype=torch.float32)
+    disk.sv_filter_backward_image(basis, g_out, d_maps, grad_in=g_in, stream=stream)
+    torch.cuda.synchronize()
+    bts = []
+    for _ in range(5):
+        flush.fill_(2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        disk.sv_filter_backward_image(basis, g_out, d_maps, grad_in=g_in, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        bts.append(a.elapsed_time(b))
+    bms = float(np.median(bts))
+    out["backward_image"] = {"value": px / (bms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": bms,
+                             "grad_in": "fp32", "grad_out": "fp16"}
+
     # dense spatially varying convolution on the same frame (Eq. 1 per pixel)
     n0 = np.linspace(2.0, 40.0, 16)
     n1 = np.linspace(0.0, 1.0, 16)
@@ -317,7 +335,7 @@ def main():
     if rank == 0:
         line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"],
                     clocks=res["clocks"], gpu_launches=res["gpu_launches"])
-        for k in ("roofline", "e2e", "dense_sv", "smem_model"):
+        for k in ("roofline", "e2e", "dense_sv", "backward_image", "smem_model"):
             if k in res:
                 line[k] = res[k]
         line["step_ms_min"] = res["step_ms_min"]

@@ -127,6 +127,24 @@ int disk_sv_filter(const disk_basis *basis, const void *d_in, size_t in_pitch,
                    int dtype, const float *d_maps, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Gradient of the spatially varying filter with respect to its input image
+ * (transpose of Eq. 3 with the Eq. 9 per-pixel complex):
+ *   d_grad_in = A_1^T A_2^T ... A_L^T d_grad_out,
+ * A_l the layer-l operator of disk_sv_filter on the same maps, basis and
+ * clamp-to-edge border (a corner clamped onto the border pixel sends its
+ * share back to that pixel).  The filter is linear in the image, so the
+ * result does not depend on the image itself.
+ * d_grad_out: H x W x C of type dtype (pitch in bytes); d_grad_in: H x W x C
+ *   float (pitch in bytes, at least W * C * 4).  Other arguments as
+ *   disk_sv_filter.  Scratch: two FP32 RGBA planes (2 * H * W * 16 bytes)
+ *   from the stream's pool.  Accumulation uses floating-point atomics, so the
+ *   last bits of the result vary from run to run. */
+int disk_sv_filter_backward_image(const disk_basis *basis, const void *d_grad_out,
+                                  size_t gout_pitch, float *d_grad_in,
+                                  size_t gin_pitch, int H, int W, int C, int dtype,
+                                  const float *d_maps, void *stream);
+
+/* ---------------------------------------------------------------------------
  * disk_sv_filter without any allocation.  The paper has no counterpart: this
  * is a deployment variant of disk_sv_filter.
  *

@@ -59,6 +59,8 @@ def lib() -> ctypes.CDLL:
             "disk_basis_info": (_i, [_vp, _ip, _ip, _ip, _ip]),
             "disk_basis_free": (None, [_vp]),
             "disk_sv_filter": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
+            "disk_sv_filter_backward_image": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp,
+                                                   _vp]),
             "disk_sv_filter_noalloc": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
             "disk_dense_sv": (_i, [_i, _ip, _fp, _vp, _i, _vp, _sz, _vp, _sz, _i, _i, _i, _i,
                                    _vp, _vp]),
@@ -194,6 +196,25 @@ def sv_filter(basis: Basis, img, maps, out=None, stream=None):
         basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
         _vp(maps.data_ptr()), _stream(stream)))
     return out
+
+
+def sv_filter_backward_image(basis: Basis, grad_out, maps, grad_in=None, stream=None):
+    """Gradient of sv_filter with respect to its input image: the transpose of
+    the cascade applied to grad_out [H, W, C] (float32 or float16); returns a
+    float32 [H, W, C] tensor."""
+    import torch
+    gp, gpitch, H, W, C = _image_args(grad_out)
+    if grad_in is None:
+        grad_in = torch.empty((H, W, C), device=grad_out.device, dtype=torch.float32)
+    ip, ipitch, *_ = _image_args(grad_in)
+    if grad_in.dtype != torch.float32 or tuple(grad_in.shape) != (H, W, C):
+        raise ValueError("grad_in must be float32 [H, W, C]")
+    if maps.dtype != torch.float32 or not maps.is_cuda or not maps.is_contiguous():
+        raise ValueError("maps must be a contiguous float32 CUDA tensor [dims, H, W]")
+    _check("disk_sv_filter_backward_image", lib().disk_sv_filter_backward_image(
+        basis.handle, _vp(gp), gpitch, _vp(ip), ipitch, H, W, C, _dtype_code(grad_out),
+        _vp(maps.data_ptr()), _stream(stream)))
+    return grad_in
 
 
 def sv_filter_noalloc(basis: Basis, img, maps, out, stream=None):

@@ -1,0 +1,87 @@
+"""GPU parity of the image gradient of the spatially varying filter against
+the oracle's transpose, and the forward/backward dot-product identity."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2512_04556_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _case(H, W, dims, seed, spread=1.5, L=3, T=5):
+    g = np.random.default_rng(seed)
+    if dims == 1:
+        axes = [[1.0, 2.0, 4.0, 8.0]]
+        th = wl.basis_random(axes[0], L, T, spread, seed)
+        maps = wl.param_map(H, W, 0.5, 9.0, 6.0, seed)[None]
+    else:
+        axes = [list(np.linspace(1.0, 3.0, 3)), list(np.linspace(0.0, 1.0, 4))]
+        th = wl.basis_random(np.repeat(np.linspace(1, 3, 3), 4), L, T, spread, seed)
+        maps = np.stack([wl.param_map(H, W, 0.8, 3.2, 6.0, seed),
+                         g.uniform(-0.1, 1.1, (H, W)).astype(np.float32)])
+    th[..., 2] = g.normal(0.2, 0.3, th[..., 2].shape)   # signed weights
+    return axes, th.astype(np.float32), maps.astype(np.float32)
+
+
+def _oracle_adjoint(gout, maps, axes, th):
+    return oracle.sv_filter_adjoint(gout.astype(np.float64), maps.astype(np.float64),
+                                    [len(a) for a in axes], np.concatenate(axes).astype(np.float64),
+                                    th.astype(np.float64))
+
+
+@pytest.mark.parametrize("dims,H,W,C,dtype", [(1, 37, 45, 3, "f32"), (2, 40, 33, 3, "f32"),
+                                             (1, 5, 70, 4, "f32"), (2, 31, 29, 3, "f16"),
+                                             (1, 64, 96, 3, "f16")])
+def test_image_gradient_matches_oracle_transpose(torch_cuda, dims, H, W, C, dtype):
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    axes, th, maps = _case(H, W, dims, H * 7 + W)
+    gout = np.random.default_rng(W).standard_normal((H, W, C)).astype(np.float32)
+    if dtype == "f16":
+        gout = gout.astype(np.float16)
+    b = disk.Basis.from_arrays(axes, th)
+    got = disk.sv_filter_backward_image(b, torch.from_numpy(gout).cuda(), torch.from_numpy(maps).cuda())
+    torch.cuda.synchronize()
+    want = _oracle_adjoint(gout, maps, axes, th)
+    err = np.abs(got.cpu().numpy() - want).max() / np.abs(want).max()
+    assert err <= TOL, err
+
+
+def test_backward_is_transpose_of_forward_on_gpu(torch_cuda):
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    H, W = 70, 90
+    axes, th, maps = _case(H, W, 2, 3, spread=3.0)
+    b = disk.Basis.from_arrays(axes, th)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((H, W, 3), device="cuda", generator=g)
+    y = torch.randn((H, W, 3), device="cuda", generator=g)
+    dm = torch.from_numpy(maps).cuda()
+    lhs = (disk.sv_filter(b, x, dm).double() * y.double()).sum().item()
+    rhs = (x.double() * disk.sv_filter_backward_image(b, y, dm).double()).sum().item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_autograd_function_image_gradient(torch_cuda):
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import autograd, disk
+    H, W = 33, 47
+    axes, th, maps = _case(H, W, 1, 9)
+    b = disk.Basis.from_arrays(axes, th)
+    img = torch.rand((H, W, 3), device="cuda", requires_grad=True)
+    dm = torch.from_numpy(maps).cuda()
+    w = torch.rand((H, W, 3), device="cuda")
+    (autograd.sv_filter(img, dm, b) * w).sum().backward()
+    want = _oracle_adjoint(w.cpu().numpy(), maps, axes, th)
+    err = np.abs(img.grad.cpu().numpy() - want).max() / np.abs(want).max()
+    assert err <= TOL
