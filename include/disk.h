@@ -144,6 +144,24 @@ int disk_sv_filter_backward_image(const disk_basis *basis, const void *d_grad_ou
                                   size_t gin_pitch, int H, int W, int C, int dtype,
                                   const float *d_maps, void *stream);
 
+/* Full backward of the spatially varying filter for training (gradients with
+ * respect to the tap weights and fractional offsets of the basis, and the
+ * input image), for the loss L = <d_grad_out, F(d_in)>:
+ *   d_grad_theta [B][L][T][3] (float, overwritten): dL/d theta_k -- each
+ *     pixel's tap gradient (d/dw = sum_c g_c s_c, d/d(dx,dy) = w sum_c g_c
+ *     ds_c/d(dx,dy), s the bilinear sample of the layer input) passed to node
+ *     k with the pixel's Eq. 9 weight alpha_k, summed over pixels;
+ *   d_grad_in (float H x W x C, may be NULL): as disk_sv_filter_backward_image.
+ * The layer inputs are recomputed from d_in by the forward kernels (nothing
+ * is stored by the forward call).  At an exact integer offset the derivative
+ * is the one-sided one of the floor convention.  Floating-point atomics: the
+ * last bits vary from run to run.  Scratch: (L-1) activation planes in the
+ * image's precision plus two FP32 RGBA planes, from the stream's pool. */
+int disk_sv_filter_backward(const disk_basis *basis, const void *d_in, size_t in_pitch,
+                            const void *d_grad_out, size_t gout_pitch, float *d_grad_in,
+                            size_t gin_pitch, float *d_grad_theta, int H, int W, int C,
+                            int dtype, const float *d_maps, void *stream);
+
 /* ---------------------------------------------------------------------------
  * disk_sv_filter without any allocation.  The paper has no counterpart: this
  * is a deployment variant of disk_sv_filter.

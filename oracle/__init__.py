@@ -58,6 +58,9 @@ def lib():
                        _ip, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
             l.orc_sv_filter.argtypes = sv_args
             l.orc_sv_filter_adjoint.argtypes = sv_args
+            l.orc_sv_filter_grad_theta.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.c_int, _dp, ctypes.c_int, _ip, _dp,
+                                                   ctypes.c_int, ctypes.c_int, _dp, _dp]
             l.orc_support_radius.argtypes = [_dp, ctypes.c_int, ctypes.c_int]
             l.orc_synth_canvas.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]
             l.orc_synth.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
@@ -169,6 +172,22 @@ def sv_filter_adjoint(g_out, maps, n_nodes, node_vals, theta) -> np.ndarray:
                                      out.ctypes.data_as(_dp))
     if rc:
         raise ValueError(f"orc_sv_filter_adjoint failed ({rc})")
+    return out
+
+
+def sv_filter_grad_theta(img, g_out, maps, n_nodes, node_vals, theta) -> np.ndarray:
+    """d<g_out, sv_filter(img)>/d theta [B][L][T][3] (Eq. 9 blend is linear in theta)."""
+    img, ip = _d(img)
+    H, W, C = img.shape
+    g, gp = _d(g_out)
+    maps, mp = _d(np.reshape(maps, (-1, H, W)))
+    nn, nnp, nv, nvp, th, thp = _basis_args(n_nodes, node_vals, theta)
+    B, L, T, _ = th.shape
+    out = np.zeros_like(th)
+    rc = lib().orc_sv_filter_grad_theta(ip, gp, H, W, C, mp, len(nn), nnp, nvp, L, T, thp,
+                                        out.ctypes.data_as(_dp))
+    if rc:
+        raise ValueError(f"orc_sv_filter_grad_theta failed ({rc})")
     return out
 
 

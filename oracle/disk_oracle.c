@@ -263,6 +263,84 @@ int orc_sv_filter_adjoint(const double *g_out, int H, int W, int C,
   return ORC_OK;
 }
 
+
+/* Gradient of L = <g_out, F(img)> with respect to the basis theta, through
+ * the spatially varying cascade: each layer's per-pixel tap (Eq. 9 blend at
+ * the pixel) receives dL/dw = sum_c G_l[x,c] s_c and dL/d(dx,dy) =
+ * w sum_c G_l[x,c] ds_c/d(dx,dy) with s the bilinear sample of the layer
+ * input, and passes it to node k with weight alpha_k(x) (Eq. 9 is linear in
+ * theta).  G_{l-1} is the transpose of layer l applied to G_l, as in
+ * orc_sv_filter_adjoint.  grad_theta [B][L][T][3] is overwritten. */
+int orc_sv_filter_grad_theta(const double *img, const double *g_out, int H, int W, int C,
+                             const double *maps, int dims, const int *n_nodes,
+                             const double *node_vals, int L, int T, const double *theta,
+                             double *grad_theta) {
+  if (H <= 0 || W <= 0 || C <= 0 || L <= 0 || T <= 0 || (dims != 1 && dims != 2))
+    return ORC_EINVAL;
+  int B = dims == 1 ? n_nodes[0] : n_nodes[0] * n_nodes[1];
+  long HW = (long)H * W, n = HW * C;
+  double *acts = (double *)malloc(sizeof(double) * n * L);
+  double *g = (double *)malloc(sizeof(double) * n);
+  double *gp = (double *)malloc(sizeof(double) * n);
+  double *taps = (double *)malloc(sizeof(double) * HW * T * 3);
+  double *alpha = (double *)malloc(sizeof(double) * HW * B);
+  if (!acts || !g || !gp || !taps || !alpha) {
+    free(acts); free(g); free(gp); free(taps); free(alpha);
+    return ORC_ENOMEM;
+  }
+  for (long px = 0; px < HW; px++) {
+    double pv[2] = {maps[px], dims == 2 ? maps[HW + px] : 0.0};
+    orc_alpha(pv, dims, n_nodes, node_vals, alpha + px * B);
+  }
+  /* forward, keeping every layer's input */
+  memcpy(acts, img, sizeof(double) * n);
+  for (int l = 0; l + 1 < L; l++) {
+    sv_layer_taps(maps, H, W, dims, n_nodes, node_vals, L, T, theta, l, taps);
+    orc_layer(acts + (long)l * n, acts + (long)(l + 1) * n, H, W, C, T, taps, (long)T * 3, 0);
+  }
+  memset(grad_theta, 0, sizeof(double) * (size_t)B * L * T * 3);
+  memcpy(g, g_out, sizeof(double) * n);
+  for (int l = L - 1; l >= 0; l--) {
+    const double *in = acts + (long)l * n;
+    sv_layer_taps(maps, H, W, dims, n_nodes, node_vals, L, T, theta, l, taps);
+    memset(gp, 0, sizeof(double) * n);
+    for (int v = 0; v < H; v++)
+      for (int u = 0; u < W; u++) {
+        long px = (long)v * W + u;
+        const double *tp = taps + px * T * 3;
+        for (int i = 0; i < T; i++) {
+          double dx = tp[3 * i], dy = tp[3 * i + 1], w = tp[3 * i + 2];
+          double gw = 0, gdx = 0, gdy = 0;
+          for (int c = 0; c < C; c++) {
+            double sdx, sdy;
+            double sv = orc_bilinear(in, H, W, C, c, v, u, dx, dy, 0, &sdx, &sdy);
+            double gc = g[px * C + c];
+            gw += gc * sv; gdx += gc * w * sdx; gdy += gc * w * sdy;
+          }
+          for (int k = 0; k < B; k++) {
+            double a = alpha[px * B + k];
+            if (a == 0.0) continue;
+            double *gt = grad_theta + (((size_t)k * L + l) * T + i) * 3;
+            gt[0] += a * gdx; gt[1] += a * gdy; gt[2] += a * gw;
+          }
+          double flx = floor(dx), fly = floor(dy);
+          double fx = dx - flx, fy = dy - fly;
+          int ix = u + (int)flx, iy = v + (int)fly;
+          double beta[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+          int cy[4] = {iy, iy, iy + 1, iy + 1}, cx[4] = {ix, ix + 1, ix, ix + 1};
+          for (int q = 0; q < 4; q++) {
+            int yy = clampi(cy[q], 0, H - 1), xx = clampi(cx[q], 0, W - 1);
+            for (int c = 0; c < C; c++)
+              gp[((long)yy * W + xx) * C + c] += w * beta[q] * g[px * C + c];
+          }
+        }
+      }
+    double *t = g; g = gp; gp = t;
+  }
+  free(acts); free(g); free(gp); free(taps); free(alpha);
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Impulse-response synthesis, Sec. 4.4 Eq. 10 (composite kernel of Eq. 4).  */
 /* ------------------------------------------------------------------------- */

@@ -61,6 +61,8 @@ def lib() -> ctypes.CDLL:
             "disk_sv_filter": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
             "disk_sv_filter_backward_image": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp,
                                                    _vp]),
+            "disk_sv_filter_backward": (_i, [_vp, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _i, _i, _i, _i,
+                                             _vp, _vp]),
             "disk_sv_filter_noalloc": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
             "disk_dense_sv": (_i, [_i, _ip, _fp, _vp, _i, _vp, _sz, _vp, _sz, _i, _i, _i, _i,
                                    _vp, _vp]),
@@ -215,6 +217,29 @@ def sv_filter_backward_image(basis: Basis, grad_out, maps, grad_in=None, stream=
         basis.handle, _vp(gp), gpitch, _vp(ip), ipitch, H, W, C, _dtype_code(grad_out),
         _vp(maps.data_ptr()), _stream(stream)))
     return grad_in
+
+
+def sv_filter_backward(basis: Basis, img, grad_out, maps, grad_img: bool = True,
+                       grad_theta: bool = True, stream=None):
+    """Gradients of <grad_out, sv_filter(img)> with respect to the image
+    (float32 [H, W, C]) and the basis theta (float32 [B, L, T, 3]); either may
+    be skipped (returned as None).  Activations are recomputed from img."""
+    import torch
+    ip, ipitch, H, W, C = _image_args(img)
+    gp, gpitch, *_ = _image_args(grad_out)
+    if grad_out.dtype != img.dtype or tuple(grad_out.shape) != tuple(img.shape):
+        raise ValueError("grad_out must match img in shape and dtype")
+    if maps.dtype != torch.float32 or not maps.is_cuda or not maps.is_contiguous():
+        raise ValueError("maps must be a contiguous float32 CUDA tensor [dims, H, W]")
+    gi = torch.empty((H, W, C), device=img.device, dtype=torch.float32) if grad_img else None
+    B = int(np.prod(basis.n_nodes))
+    gt = torch.empty((B, basis.L, basis.T, 3), device=img.device, dtype=torch.float32) if grad_theta else None
+    _check("disk_sv_filter_backward", lib().disk_sv_filter_backward(
+        basis.handle, _vp(ip), ipitch, _vp(gp), gpitch,
+        _vp(gi.data_ptr()) if gi is not None else None, W * C * 4,
+        _vp(gt.data_ptr()) if gt is not None else None, H, W, C, _dtype_code(img),
+        _vp(maps.data_ptr()), _stream(stream)))
+    return gi, gt
 
 
 def sv_filter_noalloc(basis: Basis, img, maps, out, stream=None):

@@ -389,3 +389,24 @@ def test_fitted_complex_reproduces_dense_convolution():
     out = oracle.sv_filter(img, np.zeros((1, 24, 25)), [1], [0.0], th[None])
     dense = oracle.dense_sv(img, np.zeros((1, 24, 25)), [1], [0.0], Ks[None])
     np.testing.assert_allclose(out[R:-R, R:-R], dense[R:-R, R:-R], atol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [1, 2])
+def test_sv_theta_gradient_matches_central_differences(dims):
+    """d<g, F(img)>/d theta of the spatially varying cascade against central
+    differences of the oracle's own forward (offsets kept off integers)."""
+    H, W = 9, 11
+    maps, nn, nv, th = _sv_case(H, W, 31, dims)
+    th = _away_from_integers(th, 0.1)
+    g = np.random.default_rng(32)
+    img = g.random((H, W, 2))
+    go = g.standard_normal((H, W, 2))
+    got = oracle.sv_filter_grad_theta(img, go, maps, nn, nv, th)
+    h = 1e-6
+    fd = np.zeros_like(th)
+    for idx in np.ndindex(*th.shape):
+        tp, tm = th.copy(), th.copy()
+        tp[idx] += h
+        tm[idx] -= h
+        fd[idx] = ((oracle.sv_filter(img, maps, nn, nv, tp) - oracle.sv_filter(img, maps, nn, nv, tm)) * go).sum() / (2 * h)
+    np.testing.assert_allclose(got, fd, rtol=1e-5, atol=1e-8 * np.abs(fd).max())

@@ -85,3 +85,92 @@ def test_autograd_function_image_gradient(torch_cuda):
     want = _oracle_adjoint(w.cpu().numpy(), maps, axes, th)
     err = np.abs(img.grad.cpu().numpy() - want).max() / np.abs(want).max()
     assert err <= TOL
+
+
+@pytest.mark.parametrize("dims,H,W,C", [(1, 29, 41, 3), (2, 35, 30, 3), (1, 20, 64, 4)])
+def test_theta_gradient_matches_oracle(torch_cuda, dims, H, W, C):
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    axes, th, maps = _case(H, W, dims, 40 + H)
+    rng = np.random.default_rng(41)
+    img = rng.random((H, W, C)).astype(np.float32)
+    gout = rng.standard_normal((H, W, C)).astype(np.float32)
+    b = disk.Basis.from_arrays(axes, th)
+    gi, gt = disk.sv_filter_backward(b, torch.from_numpy(img).cuda(), torch.from_numpy(gout).cuda(),
+                                     torch.from_numpy(maps).cuda())
+    torch.cuda.synchronize()
+    nn = [len(a) for a in axes]
+    nv = np.concatenate(axes).astype(np.float64)
+    want_t = oracle.sv_filter_grad_theta(img.astype(np.float64), gout.astype(np.float64),
+                                         maps.astype(np.float64), nn, nv, th.astype(np.float64))
+    err_t = np.abs(gt.cpu().numpy() - want_t).max() / np.abs(want_t).max()
+    assert err_t <= 1e-4, err_t
+    want_i = _oracle_adjoint(gout, maps, axes, th)
+    assert np.abs(gi.cpu().numpy() - want_i).max() / np.abs(want_i).max() <= TOL
+
+
+def test_theta_gradient_fp16_storage(torch_cuda):
+    """FP16 images keep FP16 activations: the gradient stays within the FP16 gate."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    H, W = 32, 48
+    axes, th, maps = _case(H, W, 2, 50)
+    rng = np.random.default_rng(51)
+    img = rng.random((H, W, 3)).astype(np.float16)
+    gout = rng.standard_normal((H, W, 3)).astype(np.float16)
+    b = disk.Basis.from_arrays(axes, th)
+    _, gt = disk.sv_filter_backward(b, torch.from_numpy(img).cuda(), torch.from_numpy(gout).cuda(),
+                                    torch.from_numpy(maps).cuda(), grad_img=False)
+    torch.cuda.synchronize()
+    want = oracle.sv_filter_grad_theta(img.astype(np.float64), gout.astype(np.float64),
+                                       maps.astype(np.float64), [3, 4],
+                                       np.concatenate(axes).astype(np.float64), th.astype(np.float64))
+    assert np.abs(gt.cpu().numpy() - want).max() / np.abs(want).max() <= 2e-3
+
+
+def test_theta_gradient_central_differences_on_gpu(torch_cuda):
+    """Central differences of the GPU forward (FP32) agree with the GPU
+    gradient on a sample of weights and offsets."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    H, W = 40, 40
+    axes, th, maps = _case(H, W, 1, 60)
+    rng = np.random.default_rng(61)
+    img = torch.from_numpy(rng.random((H, W, 3)).astype(np.float32)).cuda()
+    gout = torch.from_numpy(rng.standard_normal((H, W, 3)).astype(np.float32)).cuda()
+    dm = torch.from_numpy(maps).cuda()
+    _, gt = disk.sv_filter_backward(disk.Basis.from_arrays(axes, th), img, gout, dm, grad_img=False)
+    gt = gt.cpu().numpy()
+
+    def loss(t):
+        out = disk.sv_filter(disk.Basis.from_arrays(axes, t), img, dm)
+        return float((out.double() * gout.double()).sum().item())
+
+    # weights enter linearly (any step is exact); offsets use a small step so
+    # that few pixels see a bilinear kink between the two evaluations
+    for idx in [(0, 0, 0, 2), (1, 1, 2, 2), (2, 2, 4, 0), (3, 0, 1, 1), (1, 2, 3, 0)]:
+        h = 1e-2 if idx[3] == 2 else 1e-3
+        tp, tm = th.copy(), th.copy()
+        tp[idx] += h
+        tm[idx] -= h
+        fd = (loss(tp) - loss(tm)) / (2 * h)
+        assert abs(fd - gt[idx]) <= 2e-2 * max(abs(fd), 1e-2 * np.abs(gt).max()), (idx, fd, gt[idx])
+
+
+def test_autograd_cascade_theta_and_image(torch_cuda):
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import autograd
+    H, W = 30, 37
+    axes, th, maps = _case(H, W, 2, 70)
+    rng = np.random.default_rng(71)
+    img = torch.from_numpy(rng.random((H, W, 3)).astype(np.float32)).cuda().requires_grad_()
+    theta = torch.from_numpy(th).cuda().requires_grad_()
+    w = torch.from_numpy(rng.standard_normal((H, W, 3)).astype(np.float32)).cuda()
+    (autograd.sv_cascade(img, torch.from_numpy(maps).cuda(), theta, axes) * w).sum().backward()
+    want_t = oracle.sv_filter_grad_theta(img.detach().cpu().numpy().astype(np.float64),
+                                         w.cpu().numpy().astype(np.float64), maps.astype(np.float64),
+                                         [3, 4], np.concatenate(axes).astype(np.float64),
+                                         th.astype(np.float64))
+    assert np.abs(theta.grad.cpu().numpy() - want_t).max() / np.abs(want_t).max() <= 1e-4
+    want_i = _oracle_adjoint(w.cpu().numpy(), maps, axes, th)
+    assert np.abs(img.grad.cpu().numpy() - want_i).max() / np.abs(want_i).max() <= TOL
