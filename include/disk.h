@@ -257,6 +257,16 @@ int disk_fit(const float *d_targets, const int *sizes, int batch, int L, int T,
              uint64_t seed, float *d_theta_io, float *d_final_loss,
              float *d_loss_hist, void *stream);
 
+/* Launch-configuration autotuner of disk_fit: times the persistent fit kernel
+ * with 256, 512 and 1024 threads per target (a few steps each, from the
+ * radial initialisation) on this batch, and records the fastest for every
+ * later disk_fit with the same L, T and largest target size (in 32-pixel
+ * buckets); without a recorded choice disk_fit uses 512.  Synchronises the
+ * stream (do not call while capturing a graph).  *chosen_threads (may be
+ * NULL) receives the choice. */
+int disk_fit_autotune(const float *d_targets, const int *sizes, int batch, int L,
+                      int T, int loss, float eps, int *chosen_threads, void *stream);
+
 /* One evaluation of the fit objective and its gradient (the hand-written
  * backward of the cascade: d/dw, d/ddx, d/ddy of every tap, through the
  * adjoint of each layer), at d_theta [batch][L][T][3] (pixels, offsets

@@ -20,7 +20,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "canvas.cuh"
@@ -28,8 +31,9 @@
 namespace disk {
 namespace {
 
-constexpr int kFitThreads = 512;
+constexpr int kFitThreads = 512;      // init kernel and default fit CTA size
 constexpr int kFitWarps = kFitThreads / 32;
+constexpr int kFitMaxWarps = 32;      // largest fit CTA: 1024 threads
 
 struct FitMeta {
   long long tgt_off;     // floats into the packed targets
@@ -228,7 +232,7 @@ struct FitShared {
   float vo[kFitMaxTaps * 3];
   float g[kFitMaxTaps * 3];
   LayerExtent ext[DISK_MAX_LAYERS];
-  float red[kFitWarps];
+  float red[kFitMaxWarps];
 };
 
 // taps (pixels) from normalised parameters; layer extents from the taps.
@@ -338,7 +342,8 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
   }
 }
 
-__global__ void __launch_bounds__(kFitThreads) fit_kernel(FitArgs A) {
+template <int NT>
+__global__ void __launch_bounds__(NT) fit_kernel(FitArgs A) {
   __shared__ FitShared sh;
   const int b = A.order[blockIdx.x];
   const FitMeta m = A.meta[b];
@@ -420,6 +425,7 @@ struct FitPlan {
   std::vector<FitMeta> meta;
   std::vector<int> order;
   size_t scratch_floats = 0, idx_ints = 0, tgt_floats = 0;
+  int kmax = 0;
 };
 
 int plan_fit(const int *sizes, int batch, int L, FitPlan &plan) {
@@ -431,6 +437,7 @@ int plan_fit(const int *sizes, int batch, int L, FitPlan &plan) {
       return fail(DISK_ERR_INVALID_ARG, "target sizes must be odd and in [1, 257]");
     FitMeta &m = plan.meta[b];
     m.K = K;
+    plan.kmax = std::max(plan.kmax, K);
     const int h = (K - 1) / 2;
     m.s = (float)std::max(1, h);
     const int Hmax = (int)std::ceil(m.s) + 1;
@@ -453,10 +460,24 @@ int plan_fit(const int *sizes, int batch, int L, FitPlan &plan) {
   return DISK_OK;
 }
 
+// ---- launch-configuration autotuner ----------------------------------------------
+// The fit CTA size (256, 512 or 1024 threads per target) trades the
+// parallelism of one target's canvas sweeps against how many targets share an
+// SM.  disk_fit_autotune times each on the caller's batch and records the
+// fastest per (L, T, largest target size in 32-pixel buckets).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune;
+
+int tuned_threads(int L, int T, int kmax) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(L, T, (kmax + 31) / 32));
+  return it == g_tune.end() ? 512 : it->second;
+}
+
 int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, int steps,
             float lr0, float lr1, int init, int loss, float eps, unsigned long long seed,
             float *d_theta, float *d_loss, float *d_hist, float *d_grad, int mode,
-            cudaStream_t s) {
+            cudaStream_t s, int threads = 0) {
   if (!d_targets || !sizes || !d_theta) return fail(DISK_ERR_INVALID_ARG, "null pointer");
   if (batch < 1 || L < 1 || L > DISK_MAX_LAYERS || T < 1 || T > DISK_MAX_TAPS)
     return fail(DISK_ERR_INVALID_ARG, "batch >= 1, L in [1, 16], T in [1, 64] required");
@@ -509,7 +530,10 @@ int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, i
   if (mode == 0 && init != 0) fit_init_kernel<<<batch, kFitThreads, 0, s>>>(A, init, seed);
   e = cudaGetLastError();
   if (e == cudaSuccess) {
-    fit_kernel<<<batch, kFitThreads, 0, s>>>(A);
+    const int nt = threads > 0 ? threads : tuned_threads(L, T, plan.kmax);
+    if (nt == 256) fit_kernel<256><<<batch, 256, 0, s>>>(A);
+    else if (nt == 1024) fit_kernel<1024><<<batch, 1024, 0, s>>>(A);
+    else fit_kernel<512><<<batch, 512, 0, s>>>(A);
     e = cudaGetLastError();
   }
   cudaFreeAsync(buf, s);
@@ -538,4 +562,47 @@ extern "C" int disk_fit_loss_grad(const float *d_targets, const int *sizes, int 
   return run_fit(d_targets, sizes, batch, L, T, 0, 0.f, 0.f, 0, loss, eps, 0,
                  const_cast<float *>(d_theta), d_loss, nullptr, d_grad, 1,
                  static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int disk_fit_autotune(const float *d_targets, const int *sizes, int batch, int L, int T,
+                                 int loss, float eps, int *chosen_threads, void *stream) {
+  if (!sizes || batch < 1) return fail(DISK_ERR_INVALID_ARG, "bad batch");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float *theta = nullptr;
+  const size_t tb = (size_t)batch * L * T * 3 * sizeof(float);
+  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&theta), tb, s), "cudaMallocAsync(autotune)");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cand[3] = {256, 512, 1024};
+  float best_ms = 1e30f;
+  int best = 512, rc = DISK_OK;
+  int kmax = 0;
+  for (int b = 0; b < batch; ++b) kmax = std::max(kmax, sizes[b]);
+  for (int c = 0; c < 3 && rc == DISK_OK; ++c) {
+    // same start for every candidate: the radial initialisation, then 4 steps
+    rc = run_fit(d_targets, sizes, batch, L, T, 0, 1e-3f, 1e-4f, 1, loss, eps, 0, theta, nullptr,
+                 nullptr, nullptr, 0, s, cand[c]);
+    if (rc) break;
+    cudaEventRecord(e0, s);
+    rc = run_fit(d_targets, sizes, batch, L, T, 4, 1e-3f, 1e-4f, 0, loss, eps, 0, theta, nullptr,
+                 nullptr, nullptr, 0, s, cand[c]);
+    cudaEventRecord(e1, s);
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = cand[c]; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(theta, s);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[std::make_tuple(L, T, (kmax + 31) / 32)] = best;
+  }
+  if (chosen_threads) *chosen_threads = best;
+  return DISK_OK;
 }

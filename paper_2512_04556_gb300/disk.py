@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
             "disk_synth_kernel": (_i, [_vp, _i, _i, _i, _i, ctypes.c_float, _vp, _vp]),
             "disk_fit": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, ctypes.c_float, _i, _i,
                               ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
+            "disk_fit_autotune": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _ip, _vp]),
             "disk_fit_loss_grad": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _vp,
                                         _vp]),
         }
@@ -326,6 +327,16 @@ def fit(packed, sizes, L: int, T: int, steps: int, lr0: float = 1e-3, lr1: float
         eps, seed, _vp(theta.data_ptr()), _vp(final.data_ptr()),
         _vp(hist.data_ptr()) if hist is not None else None, _stream(stream)))
     return theta, final, hist
+
+
+def fit_autotune(packed, sizes, L: int, T: int, loss: int = LOSS_MSE, eps: float = 0.0,
+                 stream=None) -> int:
+    """Pick the fit kernel's CTA size for this batch shape; returns it."""
+    out = ctypes.c_int()
+    _check("disk_fit_autotune", lib().disk_fit_autotune(
+        _vp(packed.data_ptr()), _int_arr(sizes), len(sizes), L, T, loss, eps,
+        ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def fit_loss_grad(packed, sizes, theta, loss: int = LOSS_MSE, eps: float = 0.0, stream=None):

@@ -117,3 +117,30 @@ def test_fit_rejects_bad_arguments(torch_cuda):
         disk.fit(packed, [8, 9], 3, 8, 5)                 # even size
     with pytest.raises(disk.DiskError):
         disk.fit(packed, sizes, 16, 64, 5)                # L * T > 512
+
+
+def test_autotune_and_cuda_graph_replay(torch_cuda):
+    """The autotuner picks one of its CTA sizes, and a whole fit (plan
+    upload, sparse-sampling init, persistent kernel) captured in a CUDA graph
+    replays to exactly the eager result."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    tg = _targets(12, 9, 41, first=60)
+    packed, sizes = disk.pack_targets(tg)
+    assert disk.fit_autotune(packed, sizes, 3, 8) in (256, 512, 1024)
+    eager, eager_loss, _ = disk.fit(packed, sizes, 3, 8, 30, init=2, seed=3)
+    theta = torch.zeros_like(eager)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        disk.fit(packed, sizes, 3, 8, 1, init=2, seed=3, theta=theta)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        _, loss, _ = disk.fit(packed, sizes, 3, 8, 30, init=2, seed=3, theta=theta)
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(theta, eager)
+        assert torch.equal(loss, eager_loss)
