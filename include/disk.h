@@ -278,6 +278,49 @@ int disk_fit_loss_grad(const float *d_targets, const int *sizes, int batch, int 
                        int T, int loss, float eps, const float *d_theta,
                        float *d_loss, float *d_grad, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned initializer of the fit.  The paper initialises with Eq. 6 / Eq. 7;
+ * this network (a project addition) predicts a complex from the target so
+ * that the Eq. 4 fit starts closer to its optimum.  A multilayer perceptron:
+ * input the target area-resampled to side x side and scaled to a maximum of
+ * 1 (disk_downsample_targets), `depth` ReLU hidden layers of width `hidden`,
+ * linear output of L*T*3 values (offsets in units of the target half-width
+ * max(1, (K-1)/2), weights raw).  Parameters: a flat float array, for each
+ * layer W [n_in][n_out] row-major then b [n_out].  FP32 throughout.
+ * ------------------------------------------------------------------------- */
+
+/* Number of parameters (-1 for an invalid shape). */
+long long disk_mlp_param_count(int n_in, int hidden, int depth, int n_out);
+
+/* He-uniform weights U(+-sqrt(6 / n_in)) from SplitMix64 at counter
+ * seed + element index, zero biases. */
+int disk_mlp_init(float *d_params, int n_in, int hidden, int depth, int n_out,
+                  uint64_t seed, void *stream);
+
+/* d_y [batch][n_out] = network(d_x [batch][n_in]).  Scratch: two
+ * [batch][hidden] planes. */
+int disk_mlp_forward(const float *d_params, int n_in, int hidden, int depth,
+                     int n_out, const float *d_x, int batch, float *d_y,
+                     void *stream);
+
+/* One training step on a batch: mean squared error between network(d_x)
+ * and d_target [batch][n_out] into *d_loss (device float), its gradient by
+ * the hand-written backward pass, and one Adam update (beta 0.9 / 0.999,
+ * eps 1e-8, step counted from 1) of d_params with moments d_m, d_v (same
+ * size, caller-zeroed before the first step). */
+int disk_mlp_train_step(float *d_params, float *d_m, float *d_v, int step,
+                        float lr, int n_in, int hidden, int depth, int n_out,
+                        const float *d_x, const float *d_target, int batch,
+                        float *d_loss, void *stream);
+
+/* Area resampling of `batch` packed targets (as for disk_fit; sizes host
+ * int[batch], <= 4096) to d_out [batch][side][side], each scaled to a
+ * maximum of 1: output cell (j, i) averages the input pixels it overlaps,
+ * weighted by overlap area.  Copies the small size table from pageable host
+ * memory (not capturable in a graph). */
+int disk_downsample_targets(const float *d_targets, const int *sizes, int batch,
+                            int side, float *d_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,12 @@ def lib() -> ctypes.CDLL:
             "disk_fit": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, ctypes.c_float, _i, _i,
                               ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
             "disk_fit_autotune": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _ip, _vp]),
+            "disk_mlp_param_count": (ctypes.c_longlong, [_i, _i, _i, _i]),
+            "disk_mlp_init": (_i, [_vp, _i, _i, _i, _i, ctypes.c_uint64, _vp]),
+            "disk_mlp_forward": (_i, [_vp, _i, _i, _i, _i, _vp, _i, _vp, _vp]),
+            "disk_mlp_train_step": (_i, [_vp, _vp, _vp, _i, ctypes.c_float, _i, _i, _i, _i, _vp, _vp,
+                                         _i, _vp, _vp]),
+            "disk_downsample_targets": (_i, [_vp, _ip, _i, _i, _vp, _vp]),
             "disk_fit_loss_grad": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _vp,
                                         _vp]),
         }
@@ -349,3 +355,50 @@ def fit_loss_grad(packed, sizes, theta, loss: int = LOSS_MSE, eps: float = 0.0, 
         _vp(packed.data_ptr()), _int_arr(sizes), batch, L, T, loss, eps,
         _vp(theta.data_ptr()), _vp(l.data_ptr()), _vp(g.data_ptr()), _stream(stream)))
     return l, g
+
+
+class MLP:
+    """The learned initializer's network: parameters and Adam moments on the
+    device; shape (n_in, hidden, depth, n_out)."""
+
+    def __init__(self, n_in: int, hidden: int, depth: int, n_out: int, seed: int = 0,
+                 device="cuda"):
+        import torch
+        self.shape = (n_in, hidden, depth, n_out)
+        n = lib().disk_mlp_param_count(*self.shape)
+        if n < 0:
+            raise ValueError(f"bad MLP shape {self.shape}")
+        self.params = torch.empty(n, device=device, dtype=torch.float32)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step = 0
+        self._loss = torch.zeros(1, device=device, dtype=torch.float32)
+        _check("disk_mlp_init", lib().disk_mlp_init(_vp(self.params.data_ptr()), *self.shape,
+                                                    seed, _stream(None)))
+
+    def forward(self, x, stream=None):
+        import torch
+        y = torch.empty((x.shape[0], self.shape[3]), device=x.device, dtype=torch.float32)
+        _check("disk_mlp_forward", lib().disk_mlp_forward(
+            _vp(self.params.data_ptr()), *self.shape, _vp(x.data_ptr()), x.shape[0],
+            _vp(y.data_ptr()), _stream(stream)))
+        return y
+
+    def train_step(self, x, target, lr: float, stream=None):
+        """One Adam step on the batch; returns the loss as a device tensor."""
+        self.step += 1
+        _check("disk_mlp_train_step", lib().disk_mlp_train_step(
+            _vp(self.params.data_ptr()), _vp(self.m.data_ptr()), _vp(self.v.data_ptr()),
+            self.step, lr, *self.shape, _vp(x.data_ptr()), _vp(target.data_ptr()), x.shape[0],
+            _vp(self._loss.data_ptr()), _stream(stream)))
+        return self._loss
+
+
+def downsample_targets(packed, sizes, side: int = 64, stream=None):
+    """Area-resampled targets [batch, side, side], each scaled to max 1."""
+    import torch
+    out = torch.empty((len(sizes), side, side), device=packed.device, dtype=torch.float32)
+    _check("disk_downsample_targets", lib().disk_downsample_targets(
+        _vp(packed.data_ptr()), _int_arr(sizes), len(sizes), side, _vp(out.data_ptr()),
+        _stream(stream)))
+    return out
