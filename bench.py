@@ -32,6 +32,10 @@ BASES = os.path.join(ROOT, "tests", "golden", "bases")
 C4_BASIS = os.path.join(BASES, "ellipse8x8_L4T24.dkb")
 BYTES_PER_PX = 20.0   # fused-pass algorithmic bytes: in 6 + out 6 + 2 maps x 4
 NOMINAL_HBM_GBS = 8000.0
+# DRAM bytes (read + write) of one pass (the L = 4 sv_layer launches) of the
+# current kernel, from the ncu capture summarised in
+# profiles/sv_layer_4k_fp16_2d.md; set to None whenever the kernel changes.
+TRAFFIC_PER_PASS = 662.5e6
 
 
 def parse():
@@ -181,7 +185,7 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
     out["roofline"] = {
         "bound": "hbm", "achieved": achieved, "peak": hbm or 6800.0, "unit": "GB/s",
         "frac": achieved / (hbm or 6800.0), "peak_source": "measured" if hbm else "fallback",
-        "frac_of_nominal_8tb": achieved / NOMINAL_HBM_GBS, "traffic": None,
+        "frac_of_nominal_8tb": achieved / NOMINAL_HBM_GBS, "traffic": TRAFFIC_PER_PASS,
         "kernel": "sv_layer_kernel (all L launches of one pass)",
         "bytes_per_px": BYTES_PER_PX}
     # shared-memory bound model: every tap reads four 16-byte corners

@@ -3,10 +3,13 @@
 // DISK approximates and the speed baseline it is measured against.
 //
 // Same staging discipline as the sparse path so the comparison is fair: a
-// 32 x 32 output tile plus the kernel half-width is staged as FP32 RGBA in
-// shared memory; each lane owns one pixel and walks the support box of its
+// 32 x 32 output tile plus the kernel half-width is staged in shared memory
+// in the image's precision (FP16 RGBA for FP16 images, FP32 RGBA for FP32);
+// each lane owns one pixel and walks the support box of its
 // cell's node kernels (warp-uniform bound), reading the node kernels through
 // L1 and the image from shared memory.
+#include <type_traits>
+
 #include "sv_common.cuh"
 
 namespace disk {
@@ -44,9 +47,15 @@ __global__ void node_extent_kernel(const float *lut, int Kd, int *node_hw) {
   }
 }
 
+__device__ __forceinline__ float4 dense_px(const float4 &v) { return v; }
+__device__ __forceinline__ float4 dense_px(const uint2 &v) { return unpack_half4(v); }
+
 template <int DIMS, int KIND>
 __global__ void __launch_bounds__(kThreads) dense_sv_kernel(const __grid_constant__ DenseParams P) {
-  extern __shared__ float4 sm[];
+  // FP16 images are staged as FP16 (as the sparse filter does), FP32 as FP32.
+  using ST = typename std::conditional<KIND == PIX_F16, uint2, float4>::type;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  ST *sm = reinterpret_cast<ST *>(sm_raw);
   const int hd = P.hd, RW = P.region_w, RH = kTileH + 2 * hd;
   const int tx0 = blockIdx.x * kTileW, ty0 = blockIdx.y * kTileH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -54,7 +63,10 @@ __global__ void __launch_bounds__(kThreads) dense_sv_kernel(const __grid_constan
     const int gy = min(max(ty0 - hd + ry, 0), P.H - 1);
     for (int rx = lane; rx < RW; rx += 32) {
       const int gx = min(max(tx0 - hd + rx, 0), P.W - 1);
-      sm[ry * RW + rx] = load_px<KIND>(P.src, P.src_pitch, P.C, gy, gx);
+      if constexpr (KIND == PIX_F16)
+        sm[ry * RW + rx] = load_raw16<KIND>(P.src, P.src_pitch, P.C, gy, gx);
+      else
+        sm[ry * RW + rx] = load_px<KIND>(P.src, P.src_pitch, P.C, gy, gx);
     }
   }
   __syncthreads();
@@ -74,16 +86,16 @@ __global__ void __launch_bounds__(kThreads) dense_sv_kernel(const __grid_constan
     const float *k10 = P.lut + (size_t)cell.n10 * KK + hd * Kd + hd;
     const float *k01 = P.lut + (size_t)cell.n01 * KK + hd * Kd + hd;
     const float *k11 = P.lut + (size_t)cell.n11 * KK + hd * Kd + hd;
-    const float4 *c = sm + (r + hd) * RW + (lane + hd);
+    const ST *c = sm + (r + hd) * RW + (lane + hd);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int my = -hb; my <= hb; ++my) {
-      const float4 *row = c - my * RW;
+      const ST *row = c - my * RW;
       const int ko = my * Kd;
 #pragma unroll 4
       for (int mx = -hb; mx <= hb; ++mx) {
         float kw = cell.a00 * __ldg(k00 + ko + mx) + cell.a10 * __ldg(k10 + ko + mx);
         if (DIMS == 2) kw += cell.a01 * __ldg(k01 + ko + mx) + cell.a11 * __ldg(k11 + ko + mx);
-        const float4 v = row[-mx];  // I[x - m]: true convolution
+        const float4 v = dense_px(row[-mx]);  // I[x - m]: true convolution
         acc.x += kw * v.x; acc.y += kw * v.y; acc.z += kw * v.z; acc.w += kw * v.w;
       }
     }
@@ -102,7 +114,7 @@ int launch_dense(const DenseParams &P, cudaStream_t s) {
                   "cudaFuncSetAttribute(dense_sv)");
     attr_set |= 1ull << (dev & 63);
   }
-  const size_t smem = (size_t)P.region_w * (kTileH + 2 * P.hd) * sizeof(float4);
+  const size_t smem = (size_t)P.region_w * (kTileH + 2 * P.hd) * (KIND == PIX_F16 ? 8 : 16);
   dim3 grid((P.W + kTileW - 1) / kTileW, (P.H + kTileH - 1) / kTileH);
   k<<<grid, kThreads, smem, s>>>(P);
   DISK_TRY_CUDA(cudaGetLastError(), "launch dense_sv_kernel");

@@ -6,7 +6,8 @@
 // per-pixel taps, recomputed from the maps exactly as the forward pass does.
 // Each layer's transpose is a scatter (the taps belong to the output pixel):
 // a CTA owns a 32 x 32 tile of output pixels x, zeroes a shared-memory
-// accumulator covering the tile plus the layer halo, and for every tap adds
+// accumulator (one float plane per channel) covering the tile plus the layer
+// halo, and for every tap adds
 // w * beta_c * g[x] to the four corners x + n + c (coordinates clamped to the
 // image, which is the transpose of the clamp-to-edge read).  The region is
 // then added into the layer's FP32 RGBA gradient plane with vector global
@@ -38,12 +39,14 @@ struct BwParams {
 template <int DIMS, int GKIND, int CH>
 __global__ void __launch_bounds__(kBwThreads)
 sv_adjoint_layer_kernel(const __grid_constant__ BwParams P) {
-  extern __shared__ float4 acc[];
-  const int halo = P.halo, RW = P.region_w, RH = kBwTileH + 2 * halo;
+  // One float plane per channel: consecutive lanes add to consecutive words,
+  // so the shared-memory atomics of a warp spread over all banks.
+  extern __shared__ float acc[];
+  const int halo = P.halo, RW = P.region_w, RH = kBwTileH + 2 * halo, RN = RW * RH;
   const int tx0 = blockIdx.x * kBwTileW, ty0 = blockIdx.y * kBwTileH;
   const int ox = tx0 - halo, oy = ty0 - halo;  // image coordinates of region (0, 0)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = threadIdx.x; j < RW * RH; j += kBwThreads) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int j = threadIdx.x; j < RN * CH; j += kBwThreads) acc[j] = 0.f;
   __syncthreads();
 
   // Tiles whose region crosses the image border clamp every corner; the
@@ -80,15 +83,15 @@ sv_adjoint_layer_kernel(const __grid_constant__ BwParams P) {
           ly0 = min(max(ly0, 0), P.H - 1); ly1 = min(max(ly1, 0), P.H - 1);
         }
         lx0 -= ox; lx1 -= ox; ly0 -= oy; ly1 -= oy;
-        float *c00 = &acc[ly0 * RW + lx0].x, *c01 = &acc[ly0 * RW + lx1].x;
-        float *c10 = &acc[ly1 * RW + lx0].x, *c11 = &acc[ly1 * RW + lx1].x;
-        atomicAdd(c00, w00 * g.x); atomicAdd(c00 + 1, w00 * g.y); atomicAdd(c00 + 2, w00 * g.z);
-        atomicAdd(c01, w01 * g.x); atomicAdd(c01 + 1, w01 * g.y); atomicAdd(c01 + 2, w01 * g.z);
-        atomicAdd(c10, w10 * g.x); atomicAdd(c10 + 1, w10 * g.y); atomicAdd(c10 + 2, w10 * g.z);
-        atomicAdd(c11, w11 * g.x); atomicAdd(c11 + 1, w11 * g.y); atomicAdd(c11 + 2, w11 * g.z);
-        if (CH == 4) {
-          atomicAdd(c00 + 3, w00 * g.w); atomicAdd(c01 + 3, w01 * g.w);
-          atomicAdd(c10 + 3, w10 * g.w); atomicAdd(c11 + 3, w11 * g.w);
+        const int i00 = ly0 * RW + lx0, i01 = ly0 * RW + lx1, i10 = ly1 * RW + lx0, i11 = ly1 * RW + lx1;
+#pragma unroll
+        for (int ch = 0; ch < CH; ++ch) {
+          const float gc = ch == 0 ? g.x : ch == 1 ? g.y : ch == 2 ? g.z : g.w;
+          float *a = acc + ch * RN;
+          atomicAdd(a + i00, w00 * gc);
+          atomicAdd(a + i01, w01 * gc);
+          atomicAdd(a + i10, w10 * gc);
+          atomicAdd(a + i11, w11 * gc);
         }
       }
     }
@@ -101,7 +104,8 @@ sv_adjoint_layer_kernel(const __grid_constant__ BwParams P) {
     for (int rx = lane; rx < RW; rx += 32) {
       const int gx = ox + rx;
       if (gx < 0 || gx >= P.W) continue;
-      const float4 v = acc[ry * RW + rx];
+      const int e = ry * RW + rx;
+      const float4 v = make_float4(acc[e], acc[RN + e], acc[2 * RN + e], CH == 4 ? acc[3 * RN + e] : 0.f);
       if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f)
         atomicAdd(P.gdst + (long long)gy * P.W + gx, v);
     }
@@ -133,7 +137,7 @@ int launch_adjoint(const BwParams &P, cudaStream_t s) {
                   "cudaFuncSetAttribute(sv_adjoint)");
     attr_set |= 1ull << (dev & 63);
   }
-  const size_t smem = (size_t)P.region_w * (kBwTileH + 2 * P.halo) * sizeof(float4);
+  const size_t smem = (size_t)P.region_w * (kBwTileH + 2 * P.halo) * CH * sizeof(float);
   dim3 grid((P.W + kBwTileW - 1) / kBwTileW, (P.H + kBwTileH - 1) / kBwTileH);
   k<<<grid, kBwThreads, smem, s>>>(P);
   DISK_TRY_CUDA(cudaGetLastError(), "launch sv_adjoint_layer_kernel");

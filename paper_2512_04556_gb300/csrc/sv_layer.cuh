@@ -108,11 +108,14 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   const float magic = 12582912.0f;
   const float2 r = __fadd2_rn(__fadd2_rn(d, make_float2(-0.5f, -0.5f)), make_float2(magic, magic));
   const float2 f = __ffma2_rn(__fadd2_rn(r, make_float2(-magic, -magic)), make_float2(-1.f, -1.f), d);
-  // Convexity of Eq. 9 bounds every blended offset by the layer reach, so
-  // nx, ny already lie in [-halo, halo - 1]; the clamp only guarantees that
-  // shared memory is never read outside the staged region.
-  const int nx = min(max(__float_as_int(r.x) - 0x4B400000, -halo), halo - 1);
-  const int ny = min(max(__float_as_int(r.y) - 0x4B400000, -halo), halo - 1);
+  // In bounds by construction: the Eq. 9 weights are non-negative and sum to
+  // one within a few ulp (t is clamped to [0, 1] and p to the node range,
+  // NaN to the first node), and every node tap satisfies |o| <= R, the layer
+  // reach; so the blended |d| <= R (1 + 2^-21) and n = round(d - 1/2) lies in
+  // [-ceil(R) - 1, ceil(R)] = [-halo, halo - 1], which with the corner n + 1
+  // keeps every read inside the staged tile + halo region.
+  const int nx = __float_as_int(r.x) - 0x4B400000;
+  const int ny = __float_as_int(r.y) - 0x4B400000;
   const ST *q = base + ny * RW + nx;
   const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y);
   const float2 wy1 = __fmul2_rn(w, fy), wy0 = __ffma2_rn(wy1, make_float2(-1.f, -1.f), w);
