@@ -71,6 +71,19 @@ def c4_inputs():
     return img, np.stack([m0, m1])
 
 
+def max_over_ranks(x: float, dist) -> float:
+    """Largest value over all ranks (every rank gets it); x itself without a
+    process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampler running while the timed region runs."""
 
@@ -154,11 +167,7 @@ def run_disk(args, rank, world, dist):
     if dist:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = float(np.mean(step_ms))
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(step_ms)), dist)
     px = H * W
     value = world * px / (ms * 1e-3) / 1e9
     res = {"ms_per_step": ms, "value": value, "clocks": clk.summary(), "wall_s": wall,
