@@ -1,0 +1,151 @@
+"""Parity at the full benchmark sizes, in the launch configuration the
+benchmark times, on sampled outputs the FP64 oracle computes one by one.
+
+An output pixel of the L-layer cascade depends only on the input within
+R = sum_l (ceil(max |o_l|) + 1) of it, so the oracle filters the crop of
+radius R around each sampled pixel (clipped at the true image border, where
+clamp-to-edge then reads exactly what the full frame reads) and the GPU's
+full-frame output is compared there.  The image gradient is sampled the same
+way (its dependency cone has the same radius).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import basis_io, mlp
+from paper_2512_04556_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BASES = os.path.join(ROOT, "tests", "golden", "bases")
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _samples(H, W, n, seed):
+    g = np.random.default_rng(seed)
+    pts = [(0, 0), (H - 1, W - 1), (0, W - 1), (H - 1, 0), (H // 2, 3), (5, W // 2)]
+    pts += [(int(g.integers(0, H)), int(g.integers(0, W))) for _ in range(n - len(pts))]
+    return pts
+
+
+def _cone(theta):
+    return int(sum(np.ceil(np.abs(theta[:, l, :, :2]).max()) + 1 for l in range(theta.shape[1])))
+
+
+def _crop_oracle(fn, arr, maps, y, x, R):
+    H, W = arr.shape[:2]
+    y0, y1, x0, x1 = max(0, y - R), min(H, y + R + 1), max(0, x - R), min(W, x + R + 1)
+    out = fn(np.ascontiguousarray(arr[y0:y1, x0:x1]).astype(np.float64),
+             np.ascontiguousarray(maps[:, y0:y1, x0:x1]).astype(np.float64))
+    return out[y - y0, x - x0]
+
+
+def _frame4k():
+    H, W = wl.C4["H"], wl.C4["W"]
+    img = wl.to_fp16(wl.image_rects(H, W, 3))
+    m0 = wl.param_map(H, W, *wl.C4["map_range0"], sigma=wl.C4["map_sigma"], stream=0)
+    m1 = wl.param_map(H, W, *wl.C4["map_range1"], sigma=wl.C4["map_sigma"], stream=1)
+    return img, np.stack([m0, m1])
+
+
+def test_4k_fp16_2d_filter_sampled(torch_cuda):
+    """The benchmark frame (3840 x 2160 FP16, 8 x 8 fitted ellipses, L=4,
+    T=24), filtered exactly as bench.py does, against the oracle on crops."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    img, maps = _frame4k()
+    path = os.path.join(BASES, "ellipse8x8_L4T24.dkb")
+    b = disk.Basis.load(path)
+    out = disk.sv_filter(b, torch.from_numpy(img).cuda(), torch.from_numpy(maps).cuda()).cpu().numpy()
+    axes, th = basis_io.read(path)
+    th = th.astype(np.float64)
+    R = _cone(th)
+    nn, nv = [len(a) for a in axes], np.concatenate(axes).astype(np.float64)
+    fn = lambda a, m: oracle.sv_filter(a, m, nn, nv, th)
+    got, want = [], []
+    for (y, x) in _samples(*img.shape[:2], 24, 0):
+        want.append(np.float16(_crop_oracle(fn, img, maps, y, x, R)).astype(np.float64))
+        got.append(out[y, x].astype(np.float64))
+    got, want = np.array(got), np.array(want)
+    assert np.abs(got - want).max() / np.abs(want).max() <= 2e-3
+
+
+def test_4k_fp16_2d_image_gradient_sampled(torch_cuda):
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    img, maps = _frame4k()
+    path = os.path.join(BASES, "ellipse8x8_L4T24.dkb")
+    b = disk.Basis.load(path)
+    go = wl.to_fp16(np.random.default_rng(9).uniform(-1, 1, img.shape).astype(np.float32))
+    gi = disk.sv_filter_backward_image(b, torch.from_numpy(go).cuda(),
+                                       torch.from_numpy(maps).cuda()).cpu().numpy()
+    axes, th = basis_io.read(path)
+    th = th.astype(np.float64)
+    R = _cone(th)
+    nn, nv = [len(a) for a in axes], np.concatenate(axes).astype(np.float64)
+    fn = lambda a, m: oracle.sv_filter_adjoint(a, m, nn, nv, th)
+    got, want = [], []
+    for (y, x) in _samples(*img.shape[:2], 12, 1):
+        want.append(_crop_oracle(fn, go, maps, y, x, R))
+        got.append(gi[y, x].astype(np.float64))
+    got, want = np.array(got), np.array(want)
+    assert np.abs(got - want).max() / np.abs(want).max() <= 1e-5
+
+
+def test_1080p_fp32_1d_filter_sampled(torch_cuda):
+    """1920 x 1080 FP32, 16 fitted disks (radius 1..32), L=4, T=16."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    H, W = 1080, 1920
+    img = wl.image_rects(H, W, 3)
+    maps = wl.param_map(H, W, 1.0, 32.0, sigma=96.0)[None]
+    path = os.path.join(BASES, "disk16_L4T16.dkb")
+    b = disk.Basis.load(path)
+    out = disk.sv_filter(b, torch.from_numpy(img).cuda(), torch.from_numpy(maps).cuda()).cpu().numpy()
+    axes, th = basis_io.read(path)
+    th = th.astype(np.float64)
+    R = _cone(th)
+    fn = lambda a, m: oracle.sv_filter(a, m, [16], axes[0].astype(np.float64), th)
+    got, want = [], []
+    for (y, x) in _samples(H, W, 24, 2):
+        want.append(_crop_oracle(fn, img, maps, y, x, R))
+        got.append(out[y, x].astype(np.float64))
+    got, want = np.array(got), np.array(want)
+    assert np.abs(got - want).max() / np.abs(want).max() <= 1e-5
+
+
+def test_full_fit_batch_sampled_targets(torch_cuda):
+    """The 256-target batch fitted in one launch as the benchmark does (sparse
+    sampling, 500 steps); the oracle fits three of its targets alone.  The
+    loss histories agree to 2 % after 500 steps (FP32 vs FP64 paths)."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    tg = wl.shape_batch(256)
+    packed, sizes = disk.pack_targets(tg)
+    _, _, hist = disk.fit(packed, sizes, 4, 16, 500, init=disk.INIT_SS, seed=7, loss_hist=True)
+    hist = hist.cpu().numpy()
+    for b in np.argsort(sizes)[:3]:
+        _, wh = oracle.fit(tg[b], 4, 16, 500, init=oracle.INIT_SS, seed=7)
+        np.testing.assert_allclose(hist[b, [0, 100, 500]], wh[[0, 100, 500]], rtol=2e-2)
+
+
+def test_mlp_full_shape_forward(torch_cuda):
+    """The learned initializer's network at its full shape (4096-512-512-512-192,
+    batch 256) against the FP64 oracle."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    net = disk.MLP(4096, 512, 3, 192, seed=3)
+    x = np.random.default_rng(4).random((256, 4096)).astype(np.float32)
+    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    want, _ = mlp.forward(net.params.cpu().numpy().astype(np.float64), x.astype(np.float64),
+                          4096, 512, 3, 192)
+    assert np.abs(y - want).max() <= 1e-5 * np.abs(want).max()
