@@ -75,7 +75,7 @@ extern "C" int disk_sv_filter(const disk_basis *b, const void *d_in, size_t in_p
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
   for (int l = 0; l < b->L; ++l) {
     const int h = halo_of(b->reach[l]);
-    const size_t smem = (size_t)(kSvTileW + 2 * h) * (kSvTileH + 2 * h) * (dtype == DISK_F32 ? 16 : 8);
+    const size_t smem = (size_t)(kSvTileW + 2 * h) * (kSvTileH + 2 * h) * sv_stage_bytes(C);
     if (smem > (size_t)kSvMaxSmem) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -2,11 +2,11 @@
 // Eq. 3): the kernel template shared by the 1-D and 2-D translation units.
 //
 // Each CTA owns a 32 x 32 output tile.  It stages the layer's source region
-// (tile + the layer's halo, clamp-to-edge) into shared memory in the image's
-// storage precision -- FP32 RGBA (16 B) for FP32 images, FP16 RGBA (8 B) for
-// FP16 images, whose planes are FP16 throughout -- so each bilinear corner is
-// one vector shared load and a warp's 32 lanes (consecutive columns) read
-// consecutive entries.  Arithmetic and accumulation are FP32.
+// (tile + the layer's halo, clamp-to-edge) into shared memory as FP32 planes
+// -- (r, g) pairs in one, b (or (b, a) pairs) in another -- converting FP16
+// sources once per staged pixel instead of once per tap and corner; a warp's
+// 32 lanes (consecutive columns) read consecutive entries.  FP16 images keep
+// FP16 planes in HBM; arithmetic and accumulation are FP32.
 // Every thread owns four pixels of one column (rows r, r+8, r+16, r+24).
 // When all pixels of a warp sit in the same kernel-space cell -- the common
 // case, parameter maps being smooth -- the node taps of each tap index are
@@ -25,6 +25,9 @@ constexpr int kSvWarps = kSvThreads / 32;
 constexpr int kSvPix = kSvTileH / kSvWarps;  // pixels per thread
 constexpr int kSvParamTaps = 1792;           // 28 KB of float4, inside the 32 KB parameter limit
 constexpr int kSvMaxSmem = 232448;           // 227 KB opt-in shared memory per CTA
+
+// Shared-memory bytes per staged pixel: FP32 (r, g) + b, or (r, g) + (b, a).
+__host__ __device__ constexpr size_t sv_stage_bytes(int C) { return C == 4 ? 16 : 12; }
 
 template <int NP>
 struct SvLayerParams {
@@ -65,22 +68,23 @@ struct Acc {
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
-// Weighted corner into the accumulator, from an FP32 or FP16 staged pixel.
+// The staged region: (r, g) pairs, then b (3 channels) or (b, a) pairs.
+struct Staged {
+  const float2 *rg;
+  const float *b;     // CH == 3
+  const float2 *ba;   // CH == 4
+};
+
+// Weighted corner e of the staged region into the accumulator.
 template <int CH>
-__device__ __forceinline__ void add_corner(const float4 &v, const float2 &wb, Acc &acc) {
-  acc.rg = __ffma2_rn(wb, lo2(v), acc.rg);
-  acc.b = fmaf(wb.x, v.z, acc.b);
-  if (CH == 4) acc.a = fmaf(wb.x, v.w, acc.a);
-}
-template <int CH>
-__device__ __forceinline__ void add_corner(const uint2 &u, const float2 &wb, Acc &acc) {
-  acc.rg = __ffma2_rn(wb, __half22float2(*reinterpret_cast<const __half2 *>(&u.x)), acc.rg);
+__device__ __forceinline__ void add_corner(const Staged &st, int e, const float2 &wb, Acc &acc) {
+  acc.rg = __ffma2_rn(wb, st.rg[e], acc.rg);
   if (CH == 4) {
-    const float2 ba = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    const float2 ba = st.ba[e];
     acc.b = fmaf(wb.x, ba.x, acc.b);
     acc.a = fmaf(wb.x, ba.y, acc.a);
   } else {
-    acc.b = fmaf(wb.x, __low2float(*reinterpret_cast<const __half2 *>(&u.y)), acc.b);
+    acc.b = fmaf(wb.x, st.b[e], acc.b);
   }
 }
 
@@ -88,10 +92,10 @@ __device__ __forceinline__ void add_corner(const uint2 &u, const float2 &wb, Acc
 // the pixel's weights, the integer/fraction split of the offset, and the
 // Eq. 2 bilinear sample from the staged region, all in packed FP32 pairs:
 // (dx, dy) and the corner weights travel as pairs, colour as (r, g) + b.
-template <int DIMS, int CH, typename ST>
+template <int DIMS, int CH>
 __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, const float4 &q01,
-                                       const float4 &q11, const CellPairs &a, const ST *base,
-                                       int RW, int halo, Acc &acc) {
+                                       const float4 &q11, const CellPairs &a, const Staged &st,
+                                       int base, int RW, Acc &acc) {
   float2 d = __fmul2_rn(a.a00, lo2(q00));
   float2 w = __fmul2_rn(a.a00, hi2(q00));
   d = __ffma2_rn(a.a10, lo2(q10), d);
@@ -116,25 +120,25 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   // keeps every read inside the staged tile + halo region.
   const int nx = __float_as_int(r.x) - 0x4B400000;
   const int ny = __float_as_int(r.y) - 0x4B400000;
-  const ST *q = base + ny * RW + nx;
+  const int e = base + ny * RW + nx;
   const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y);
   const float2 wy1 = __fmul2_rn(w, fy), wy0 = __ffma2_rn(wy1, make_float2(-1.f, -1.f), w);
   const float2 w11 = __fmul2_rn(wy1, fx), w10 = __ffma2_rn(w11, make_float2(-1.f, -1.f), wy1);
   const float2 w01 = __fmul2_rn(wy0, fx), w00 = __ffma2_rn(w01, make_float2(-1.f, -1.f), wy0);
-  add_corner<CH>(q[0], w00, acc);
-  add_corner<CH>(q[1], w01, acc);
-  add_corner<CH>(q[RW], w10, acc);
-  add_corner<CH>(q[RW + 1], w11, acc);
+  add_corner<CH>(st, e, w00, acc);
+  add_corner<CH>(st, e + 1, w01, acc);
+  add_corner<CH>(st, e + RW, w10, acc);
+  add_corner<CH>(st, e + RW + 1, w11, acc);
 }
 
 template <int DIMS, int SRC, int DST, int NP, int CH>
 __global__ void __launch_bounds__(kSvThreads, 3)
 sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
-  constexpr bool kHalf = SRC == PIX_F16 || SRC == PIX_RGBA16;
-  using ST = typename std::conditional<kHalf, uint2, float4>::type;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  ST *sm = reinterpret_cast<ST *>(sm_raw);
-  const int halo = P.halo, RW = P.region_w, RH = kSvTileH + 2 * halo;
+  const int halo = P.halo, RW = P.region_w, RH = kSvTileH + 2 * halo, RN = RW * RH;
+  float2 *s_rg = reinterpret_cast<float2 *>(sm_raw);
+  float *s_b = reinterpret_cast<float *>(sm_raw + (size_t)RN * sizeof(float2));
+  float2 *s_ba = reinterpret_cast<float2 *>(sm_raw + (size_t)RN * sizeof(float2));
   const int tx0 = blockIdx.x * kSvTileW, ty0 = blockIdx.y * kSvTileH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -144,20 +148,22 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     const int gy = min(max(ty0 - halo + ry, 0), P.H - 1);
     for (int rx = lane; rx < RW; rx += 32) {
       const int gx = min(max(tx0 - halo + rx, 0), P.W - 1);
-      if constexpr (kHalf)
-        sm[ry * RW + rx] = load_raw16<SRC>(P.src, P.src_pitch, P.C, gy, gx);
-      else
-        sm[ry * RW + rx] = load_px<SRC>(P.src, P.src_pitch, P.C, gy, gx);
+      const float4 v = load_px<SRC>(P.src, P.src_pitch, P.C, gy, gx);
+      const int e = ry * RW + rx;
+      s_rg[e] = make_float2(v.x, v.y);
+      if (CH == 4) s_ba[e] = make_float2(v.z, v.w);
+      else s_b[e] = v.z;
     }
   }
   __syncthreads();
+  const Staged st{s_rg, s_b, s_ba};
 
   const int x = tx0 + lane, xc = min(x, P.W - 1);
   const long long HW = (long long)P.H * P.W;
   const int T = P.T;
   Cell c[kSvPix];
   CellPairs cp[kSvPix];
-  const ST *base[kSvPix];
+  int base[kSvPix];
   Acc acc[kSvPix];
   bool same = true;
 #pragma unroll
@@ -166,7 +172,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     const int yc = min(ty0 + r, P.H - 1);
     c[j] = make_cell<DIMS>(P.ax, P.maps, HW, (long long)yc * P.W + xc);
     cp[j] = cell_pairs(c[j]);
-    base[j] = sm + (r + halo) * RW + (lane + halo);
+    base[j] = (r + halo) * RW + (lane + halo);
     acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
     same = same && (c[j].n00 == c[0].n00);
   }
@@ -179,7 +185,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
       const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
       const float4 q11 = DIMS == 2 ? node_tap(P, b11 + i) : q10;
 #pragma unroll
-      for (int j = 0; j < kSvPix; ++j) sv_tap<DIMS, CH, ST>(q00, q10, q01, q11, cp[j], base[j], RW, halo, acc[j]);
+      for (int j = 0; j < kSvPix; ++j) sv_tap<DIMS, CH>(q00, q10, q01, q11, cp[j], st, base[j], RW, acc[j]);
     }
   } else {
     // unrolled so the per-pixel arrays stay in registers
@@ -191,7 +197,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
         const float4 q00 = node_tap(P, b00 + i), q10 = node_tap(P, b10 + i);
         const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
         const float4 q11 = DIMS == 2 ? node_tap(P, b11 + i) : q10;
-        sv_tap<DIMS, CH, ST>(q00, q10, q01, q11, cp[j], base[j], RW, halo, acc[j]);
+        sv_tap<DIMS, CH>(q00, q10, q01, q11, cp[j], st, base[j], RW, acc[j]);
       }
     }
   }
@@ -209,8 +215,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
 template <int DIMS, int SRC, int DST, int NP, int CH>
 int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
   auto k = sv_layer_kernel<DIMS, SRC, DST, NP, CH>;
-  const size_t px_bytes = (SRC == PIX_F16 || SRC == PIX_RGBA16) ? 8 : 16;
-  const size_t smem = (size_t)P.region_w * (kSvTileH + 2 * P.halo) * px_bytes;
+  const size_t smem = (size_t)P.region_w * (kSvTileH + 2 * P.halo) * sv_stage_bytes(CH);
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
   int dev = 0;
   cudaGetDevice(&dev);
