@@ -35,7 +35,7 @@ NOMINAL_HBM_GBS = 8000.0
 # DRAM bytes (read + write) of one pass (the L = 4 sv_layer launches) of the
 # current kernel, from the ncu capture summarised in
 # profiles/sv_layer_4k_fp16_2d.md; set to None whenever the kernel changes.
-TRAFFIC_PER_PASS = 662.5e6
+TRAFFIC_PER_PASS = 667.8e6
 
 
 def parse():
@@ -146,6 +146,8 @@ def run_disk(args, rank, world, dist):
     def step():
         disk.sv_filter(basis, d_img, d_maps, out=d_out, stream=stream)
 
+    # tile configuration picked by the library's autotuner for this frame shape
+    tile_pix = disk.sv_filter_autotune(basis, d_img, d_maps, out=d_out, stream=stream)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -171,6 +173,7 @@ def run_disk(args, rank, world, dist):
     px = H * W
     value = world * px / (ms * 1e-3) / 1e9
     res = {"ms_per_step": ms, "value": value, "clocks": clk.summary(), "wall_s": wall,
+           "tile": f"32x{8 * tile_pix} ({tile_pix} px/thread, autotuned)",
            "gpu_launches": K * basis.L, "step_ms_min": float(np.min(step_ms)),
            "step_ms_median": float(np.median(step_ms))}
     if rank == 0 and not args.no_extras:
@@ -419,6 +422,7 @@ def main():
         for k in ("roofline", "e2e", "dense_sv", "backward_image", "fit", "smem_model"):
             if k in res:
                 line[k] = res[k]
+        line["config"]["tile"] = res["tile"]
         line["step_ms_min"] = res["step_ms_min"]
         line["step_ms_median"] = res["step_ms_median"]
         if not args.no_extras and world == 1:

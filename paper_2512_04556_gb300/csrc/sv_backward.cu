@@ -409,8 +409,8 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
           const float *t = &b->theta[(((size_t)k * b->L + l) * b->T + i) * 3];
           P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
         }
-    const int rc = b->dims == 1 ? launch_sv_layer<1, NP>(l == 0 ? user : mid, mid, C, P, s)
-                                : launch_sv_layer<2, NP>(l == 0 ? user : mid, mid, C, P, s);
+    const int rc = b->dims == 1 ? launch_sv_layer<1, NP>(l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix)
+                                : launch_sv_layer<2, NP>(l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix);
     if (rc) return rc;
   }
   return DISK_OK;

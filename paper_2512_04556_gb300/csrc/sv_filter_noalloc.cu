@@ -71,8 +71,8 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
           P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
         }
     }
-    rc = b->dims == 1 ? launch_sv_layer<1, NP>(src, dst, C, P, s)
-                      : launch_sv_layer<2, NP>(src, dst, C, P, s);
+    rc = b->dims == 1 ? launch_sv_layer<1, NP>(src, dst, C, P, s, kSvDefaultPix)
+                      : launch_sv_layer<2, NP>(src, dst, C, P, s, kSvDefaultPix);
   }
   return rc;
 }
@@ -95,7 +95,7 @@ extern "C" int disk_sv_filter_noalloc(const disk_basis *b, const void *d_in, siz
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
   for (int l = 0; l < b->L; ++l) {
     const int h = halo_of(b->reach[l]);
-    const size_t smem = (size_t)(kSvTileW + 2 * h) * (kSvTileH + 2 * h) * sv_stage_bytes(C);
+    const size_t smem = (size_t)(kSvTileW + 2 * h) * (sv_tile_h(kSvDefaultPix) + 2 * h) * sv_stage_bytes(C);
     if (smem > (size_t)kSvMaxSmem) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
   }
   float4 *planes = nullptr;

@@ -7,7 +7,7 @@
 // sources once per staged pixel instead of once per tap and corner; a warp's
 // 32 lanes (consecutive columns) read consecutive entries.  FP16 images keep
 // FP16 planes in HBM; arithmetic and accumulation are FP32.
-// Every thread owns four pixels of one column (rows r, r+8, r+16, r+24).
+// Every thread owns PIX pixels of one column (rows r, r+8, ...).
 // When all pixels of a warp sit in the same kernel-space cell -- the common
 // case, parameter maps being smooth -- the node taps of each tap index are
 // fetched once (warp-uniform constant-bank loads) and blended for the four
@@ -20,9 +20,13 @@
 
 namespace disk {
 
-constexpr int kSvTileW = 32, kSvTileH = 32, kSvThreads = 256;
+// Tile configurations: 32 columns x (8 warps x PIX rows); PIX pixels per
+// thread.  PIX = 4 (32 x 32 tiles, 3 CTAs per SM) or PIX = 2 (32 x 16 tiles,
+// 4 CTAs per SM); disk_sv_filter_autotune picks per frame shape.
+constexpr int kSvTileW = 32, kSvThreads = 256;
 constexpr int kSvWarps = kSvThreads / 32;
-constexpr int kSvPix = kSvTileH / kSvWarps;  // pixels per thread
+constexpr int kSvDefaultPix = 2;
+__host__ __device__ constexpr int sv_tile_h(int pix) { return pix * kSvWarps; }
 constexpr int kSvParamTaps = 1792;           // 28 KB of float4, inside the 32 KB parameter limit
 constexpr int kSvMaxSmem = 232448;           // 227 KB opt-in shared memory per CTA
 
@@ -131,9 +135,10 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   add_corner<CH>(st, e + RW + 1, w11, acc);
 }
 
-template <int DIMS, int SRC, int DST, int NP, int CH>
-__global__ void __launch_bounds__(kSvThreads, 3)
+template <int DIMS, int SRC, int DST, int NP, int CH, int PIX>
+__global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : 3)
 sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
+  constexpr int kSvPix = PIX, kSvTileH = PIX * kSvWarps;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int halo = P.halo, RW = P.region_w, RH = kSvTileH + 2 * halo, RN = RW * RH;
   float2 *s_rg = reinterpret_cast<float2 *>(sm_raw);
@@ -212,9 +217,10 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   }
 }
 
-template <int DIMS, int SRC, int DST, int NP, int CH>
+template <int DIMS, int SRC, int DST, int NP, int CH, int PIX>
 int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
-  auto k = sv_layer_kernel<DIMS, SRC, DST, NP, CH>;
+  auto k = sv_layer_kernel<DIMS, SRC, DST, NP, CH, PIX>;
+  constexpr int kSvTileH = PIX * kSvWarps;
   const size_t smem = (size_t)P.region_w * (kSvTileH + 2 * P.halo) * sv_stage_bytes(CH);
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
   int dev = 0;
@@ -230,19 +236,25 @@ int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
   return DISK_OK;
 }
 
-// Storage combination of one layer: (source kind, destination kind).
+// Storage combination of one layer: (source kind, destination kind), tile
+// configuration pix (2 or 4 pixels per thread).
 template <int DIMS, int NP>
-int launch_sv_layer(int src, int dst, int C, const SvLayerParams<NP> &P, cudaStream_t s);
+int launch_sv_layer(int src, int dst, int C, const SvLayerParams<NP> &P, cudaStream_t s, int pix);
 
 #define DISK_SV_CASE(DIMS, NP, S, D)                                                        \
-  if (src == S && dst == D)                                                                 \
-    return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4>(P, s) : launch_sv_layer_t<DIMS, S, D, NP, 3>(P, s);
+  if (src == S && dst == D) {                                                               \
+    if (pix == 4)                                                                           \
+      return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4, 4>(P, s)                             \
+                : launch_sv_layer_t<DIMS, S, D, NP, 3, 4>(P, s);                            \
+    return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4, 2>(P, s)                               \
+              : launch_sv_layer_t<DIMS, S, D, NP, 3, 2>(P, s);                              \
+  }
 
 // FP32 images: FP32 planes; FP16 images: FP16 planes (see intermediate_kind).
 #define DISK_SV_INSTANTIATE(DIMS, NP)                                                       \
   template <>                                                                               \
   int launch_sv_layer<DIMS, NP>(int src, int dst, int C, const SvLayerParams<NP> &P,          \
-                                cudaStream_t s) {                                           \
+                                cudaStream_t s, int pix) {                                  \
     const bool c4 = C == 4;                                                                 \
     DISK_SV_CASE(DIMS, NP, PIX_F32, PIX_RGBA32)                                             \
     DISK_SV_CASE(DIMS, NP, PIX_RGBA32, PIX_RGBA32)                                          \

@@ -63,6 +63,8 @@ def lib() -> ctypes.CDLL:
                                                    _vp]),
             "disk_sv_filter_backward": (_i, [_vp, _vp, _sz, _vp, _sz, _vp, _sz, _vp, _i, _i, _i, _i,
                                              _vp, _vp]),
+            "disk_sv_filter_autotune": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _ip, _vp]),
+            "disk_sv_filter_set_tile": (_i, [_vp, _i, _i, _i, _i, _i]),
             "disk_sv_filter_noalloc": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
             "disk_dense_sv": (_i, [_i, _ip, _fp, _vp, _i, _vp, _sz, _vp, _sz, _i, _i, _i, _i,
                                    _vp, _vp]),
@@ -205,6 +207,26 @@ def sv_filter(basis: Basis, img, maps, out=None, stream=None):
         basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
         _vp(maps.data_ptr()), _stream(stream)))
     return out
+
+
+def sv_filter_autotune(basis: Basis, img, maps, out=None, stream=None) -> int:
+    """Time the built tile configurations on this frame shape, record the
+    fastest in the basis; returns the pixels per thread chosen."""
+    import torch
+    ip, ipitch, H, W, C = _image_args(img)
+    if out is None:
+        out = torch.empty_like(img, memory_format=torch.contiguous_format)
+    op, opitch, *_ = _image_args(out)
+    chosen = ctypes.c_int()
+    _check("disk_sv_filter_autotune", lib().disk_sv_filter_autotune(
+        basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
+        _vp(maps.data_ptr()), ctypes.byref(chosen), _stream(stream)))
+    return chosen.value
+
+
+def sv_filter_set_tile(basis: Basis, H: int, W: int, C: int, dtype: int, pix: int):
+    """Record the tile configuration (2 or 4 pixels per thread) for a frame shape."""
+    _check("disk_sv_filter_set_tile", lib().disk_sv_filter_set_tile(basis.handle, H, W, C, dtype, pix))
 
 
 def sv_filter_backward_image(basis: Basis, grad_out, maps, grad_in=None, stream=None):

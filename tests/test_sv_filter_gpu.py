@@ -229,3 +229,32 @@ def test_synth_flags_taps_beyond_declared_reach(torch_cuda):
     th[1, 0, 0, 0] = 5.0
     out = disk.synth_kernel(torch.from_numpy(th).cuda(), 9, max_reach=2.0).cpu().numpy()
     assert np.isfinite(out[0]).all() and np.isnan(out[1]).all()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_tile_configurations_and_autotune(torch_cuda, dtype):
+    """Both tile configurations match the oracle and each other bit for bit;
+    the autotuner picks one of them."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    n0, n1 = 3, 3
+    axes = [list(np.linspace(2.0, 8.0, n0)), list(np.linspace(0.0, 1.0, n1))]
+    th = wl.basis_random(np.repeat(np.linspace(0.5, 1.5, n0), n1), 3, 6, 3.0, seed=70)
+    H, W = 83, 97
+    img = wl.image_uniform(H, W, 3, seed=71)
+    if dtype == "f16":
+        img = wl.to_fp16(img)
+    maps = _maps(H, W, 1.0, 9.0, 72, dims=2)
+    b = disk.Basis.from_arrays(axes, th)
+    t = torch.from_numpy(img).cuda()
+    m = torch.from_numpy(maps).cuda()
+    outs = {}
+    for pix in (2, 4):
+        disk.sv_filter_set_tile(b, H, W, 3, 0 if dtype == "f32" else 1, pix)
+        outs[pix] = disk.sv_filter(b, t, m).cpu().numpy()
+    assert np.array_equal(outs[2], outs[4])
+    want = oracle_filter(img, maps, axes, th)
+    if dtype == "f16":
+        want = want.astype(np.float16).astype(np.float64)
+    assert rel_err(outs[2], want) <= (TOL32 if dtype == "f32" else TOL16)
+    assert disk.sv_filter_autotune(b, t, m) in (2, 4)
