@@ -173,7 +173,7 @@ def run_disk(args, rank, world, dist):
     px = H * W
     value = world * px / (ms * 1e-3) / 1e9
     res = {"ms_per_step": ms, "value": value, "clocks": clk.summary(), "wall_s": wall,
-           "tile": f"32x{8 * tile_pix} ({tile_pix} px/thread, autotuned)",
+           "tile": "per layer (autotuned): " + ", ".join(f"32x{8 * p}" for p in tile_pix),
            "gpu_launches": K * basis.L, "step_ms_min": float(np.min(step_ms)),
            "step_ms_median": float(np.median(step_ms))}
     if rank == 0 and not args.no_extras:

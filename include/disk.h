@@ -192,17 +192,18 @@ int disk_sv_filter_noalloc(const disk_basis *basis, const void *d_in,
 
 /* Tile autotuner of disk_sv_filter: runs the filter on these buffers with
  * each built tile configuration (2 or 4 pixels per thread: 32 x 16 or
- * 32 x 32 output tiles), times each, and records the fastest in the basis
+ * 32 x 32 output tiles), times every layer of each (the best tile depends
+ * on the layer's halo), and records the fastest per layer in the basis
  * handle for this (H, W, C, dtype); later disk_sv_filter calls with that
- * shape use it (without a record: 32 x 16).  Writes d_out.  Synchronises the
- * stream (do not call while capturing a graph).  *chosen (may be NULL)
- * receives the pixels per thread chosen. */
+ * shape use it (without a record: 32 x 16 everywhere).  Writes d_out.
+ * Synchronises the stream (do not call while capturing a graph).  chosen
+ * (may be NULL; int[L]) receives the pixels per thread of every layer. */
 int disk_sv_filter_autotune(const disk_basis *basis, const void *d_in, size_t in_pitch,
                             void *d_out, size_t out_pitch, int H, int W, int C,
                             int dtype, const float *d_maps, int *chosen, void *stream);
 
-/* Records a tile configuration (pixels per thread: 2 or 4) for this
- * (H, W, C, dtype) in the basis handle, as disk_sv_filter_autotune does. */
+/* Records one tile configuration (pixels per thread: 2 or 4) for every
+ * layer, for this (H, W, C, dtype), in the basis handle. */
 int disk_sv_filter_set_tile(const disk_basis *basis, int H, int W, int C, int dtype,
                             int pix);
 

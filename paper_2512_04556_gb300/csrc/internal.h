@@ -22,10 +22,10 @@ struct disk_basis {
   std::vector<float> reach;      // [L]: max over nodes, taps of max(|dx|,|dy|)
   int device = 0;
   float4 *d_taps = nullptr;      // [L][B][T] = (dx, dy, w, w)
-  // filter tile configuration chosen by disk_sv_filter_autotune, per
-  // (H, W, C, dtype); read by disk_sv_filter
+  // filter tile configuration (pixels per thread) of every layer, chosen by
+  // disk_sv_filter_autotune per (H, W, C, dtype); read by disk_sv_filter
   mutable std::mutex tune_mu;
-  mutable std::map<std::tuple<int, int, int, int>, int> tune_pix;
+  mutable std::map<std::tuple<int, int, int, int>, std::vector<int>> tune_pix;
 };
 
 namespace disk {

@@ -12,7 +12,7 @@ namespace {
 template <int NP>
 int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
-               cudaStream_t s, int pix) {
+               cudaStream_t s, const int *pix, cudaEvent_t *ev) {
   // The parameter block is large; keep it off the host stack.
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
@@ -52,26 +52,34 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
           P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
         }
     }
-    rc = b->dims == 1 ? launch_sv_layer<1, NP>(src, dst, C, P, s, pix)
-                      : launch_sv_layer<2, NP>(src, dst, C, P, s, pix);
+    if (ev) cudaEventRecord(ev[l], s);
+    rc = b->dims == 1 ? launch_sv_layer<1, NP>(src, dst, C, P, s, pix[l])
+                      : launch_sv_layer<2, NP>(src, dst, C, P, s, pix[l]);
   }
+  if (ev && rc == DISK_OK) cudaEventRecord(ev[L], s);
   for (int i = 0; i < nbuf; ++i) cudaFreeAsync(bufs[i], s);
   return rc;
 }
 
-bool fits(const disk_basis *b, int C, int pix) {
-  for (int l = 0; l < b->L; ++l) {
-    const int h = halo_of(b->reach[l]);
-    const size_t smem = (size_t)(kSvTileW + 2 * h) * (sv_tile_h(pix) + 2 * h) * sv_stage_bytes(C);
-    if (smem > (size_t)kSvMaxSmem) return false;
-  }
-  return true;
+bool fits_layer(const disk_basis *b, int C, int l, int pix) {
+  const int h = halo_of(b->reach[l]);
+  const size_t smem = (size_t)(kSvTileW + 2 * h) * (sv_tile_h(pix) + 2 * h) * sv_stage_bytes(C);
+  return smem <= (size_t)kSvMaxSmem;
 }
 
-int tuned_pix(const disk_basis *b, int H, int W, int C, int dtype) {
-  std::lock_guard<std::mutex> lock(b->tune_mu);
-  auto it = b->tune_pix.find(std::make_tuple(H, W, C, dtype));
-  return it == b->tune_pix.end() ? kSvDefaultPix : it->second;
+// Per-layer tile configuration for this frame shape: the recorded one, or
+// the default, with any layer whose halo does not fit falling back to the
+// smaller tile.
+std::vector<int> layer_pix(const disk_basis *b, int H, int W, int C, int dtype) {
+  std::vector<int> pix(b->L, kSvDefaultPix);
+  {
+    std::lock_guard<std::mutex> lock(b->tune_mu);
+    auto it = b->tune_pix.find(std::make_tuple(H, W, C, dtype));
+    if (it != b->tune_pix.end() && (int)it->second.size() == b->L) pix = it->second;
+  }
+  for (int l = 0; l < b->L; ++l)
+    if (!fits_layer(b, C, l, pix[l])) pix[l] = 2;
+  return pix;
 }
 
 int check_filter_args(const disk_basis *b, const void *d_in, size_t in_pitch, const void *d_out,
@@ -82,15 +90,17 @@ int check_filter_args(const disk_basis *b, const void *d_in, size_t in_pitch, co
   int dev = 0;
   DISK_TRY_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
+  for (int l = 0; l < b->L; ++l)
+    if (!fits_layer(b, C, l, 2)) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
   return DISK_OK;
 }
 
 int filter_with(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                 size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
-                cudaStream_t s, int pix) {
+                cudaStream_t s, const int *pix, cudaEvent_t *ev = nullptr) {
   if ((size_t)b->B * b->T <= (size_t)kSvParamTaps)
-    return run_filter<kSvParamTaps>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix);
-  return run_filter<0>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix);
+    return run_filter<kSvParamTaps>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix, ev);
+  return run_filter<0>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix, ev);
 }
 
 }  // namespace
@@ -103,11 +113,9 @@ extern "C" int disk_sv_filter(const disk_basis *b, const void *d_in, size_t in_p
                               const float *d_maps, void *stream) {
   int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps);
   if (rc) return rc;
-  int pix = tuned_pix(b, H, W, C, dtype);
-  if (!fits(b, C, pix)) pix = 2;
-  if (!fits(b, C, pix)) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
+  const std::vector<int> pix = layer_pix(b, H, W, C, dtype);
   return filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps,
-                     static_cast<cudaStream_t>(stream), pix);
+                     static_cast<cudaStream_t>(stream), pix.data());
 }
 
 extern "C" int disk_sv_filter_autotune(const disk_basis *b, const void *d_in, size_t in_pitch,
@@ -117,45 +125,46 @@ extern "C" int disk_sv_filter_autotune(const disk_basis *b, const void *d_in, si
   int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaEvent_t e0, e1;
-  DISK_TRY_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
-  cudaEventCreate(&e1);
-  int best = -1;
-  float best_ms = 1e30f;
+  const int L = b->L;
+  std::vector<cudaEvent_t> ev(L + 1);
+  for (auto &e : ev) DISK_TRY_CUDA(cudaEventCreate(&e), "cudaEventCreate");
   const int cand[2] = {2, 4};
+  std::vector<float> best_ms(L, 1e30f);
+  std::vector<int> best(L, 2);
   for (int c = 0; c < 2 && rc == DISK_OK; ++c) {
-    if (!fits(b, C, cand[c])) continue;
-    rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, cand[c]);
-    float ms_min = 1e30f;
+    std::vector<int> pix(L);
+    for (int l = 0; l < L; ++l) pix[l] = fits_layer(b, C, l, cand[c]) ? cand[c] : 2;
+    rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix.data());
     for (int r = 0; r < 3 && rc == DISK_OK; ++r) {
-      cudaEventRecord(e0, s);
-      rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, cand[c]);
-      cudaEventRecord(e1, s);
-      cudaError_t e = cudaEventSynchronize(e1);
+      rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix.data(),
+                       ev.data());
+      cudaError_t e = cudaEventSynchronize(ev[L]);
       if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms_min = fminf(ms_min, ms);
+      for (int l = 0; l < L; ++l) {
+        if (pix[l] != cand[c]) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[l], ev[l + 1]);
+        if (ms < best_ms[l]) { best_ms[l] = ms; best[l] = cand[c]; }
+      }
     }
-    if (rc == DISK_OK && ms_min < best_ms) { best_ms = ms_min; best = cand[c]; }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (auto &e : ev) cudaEventDestroy(e);
   if (rc) return rc;
-  if (best < 0) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
   {
     std::lock_guard<std::mutex> lock(b->tune_mu);
     b->tune_pix[std::make_tuple(H, W, C, dtype)] = best;
   }
-  if (chosen) *chosen = best;
+  if (chosen) for (int l = 0; l < L; ++l) chosen[l] = best[l];
   return DISK_OK;
 }
 
 extern "C" int disk_sv_filter_set_tile(const disk_basis *b, int H, int W, int C, int dtype, int pix) {
   if (!b) return fail(DISK_ERR_INVALID_ARG, "null basis");
   if (pix != 2 && pix != 4) return fail(DISK_ERR_INVALID_ARG, "pixels per thread must be 2 or 4");
-  if (!fits(b, C, pix)) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory for this tile");
+  for (int l = 0; l < b->L; ++l)
+    if (!fits_layer(b, C, l, pix))
+      return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory for this tile");
   std::lock_guard<std::mutex> lock(b->tune_mu);
-  b->tune_pix[std::make_tuple(H, W, C, dtype)] = pix;
+  b->tune_pix[std::make_tuple(H, W, C, dtype)] = std::vector<int>(b->L, pix);
   return DISK_OK;
 }

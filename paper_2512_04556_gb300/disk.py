@@ -209,19 +209,19 @@ def sv_filter(basis: Basis, img, maps, out=None, stream=None):
     return out
 
 
-def sv_filter_autotune(basis: Basis, img, maps, out=None, stream=None) -> int:
+def sv_filter_autotune(basis: Basis, img, maps, out=None, stream=None) -> list:
     """Time the built tile configurations on this frame shape, record the
-    fastest in the basis; returns the pixels per thread chosen."""
+    fastest of every layer in the basis; returns pixels per thread per layer."""
     import torch
     ip, ipitch, H, W, C = _image_args(img)
     if out is None:
         out = torch.empty_like(img, memory_format=torch.contiguous_format)
     op, opitch, *_ = _image_args(out)
-    chosen = ctypes.c_int()
+    chosen = (ctypes.c_int * basis.L)()
     _check("disk_sv_filter_autotune", lib().disk_sv_filter_autotune(
         basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
-        _vp(maps.data_ptr()), ctypes.byref(chosen), _stream(stream)))
-    return chosen.value
+        _vp(maps.data_ptr()), chosen, _stream(stream)))
+    return list(chosen)
 
 
 def sv_filter_set_tile(basis: Basis, H: int, W: int, C: int, dtype: int, pix: int):
