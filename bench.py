@@ -270,11 +270,57 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
     dd = d_dense.float()
     mse = float(((o - dd) ** 2).mean().item())
     out["fit"] = fit_leg(stream)
+    out["gaussian_tilt_shift"] = gaussian_leg(d_img, flush, stream)
     out["dense_sv"] = {"value": px / (dms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": dms,
                        "kernel_max": "81x81", "lut": "16x16 ellipse grid",
                        "speedup_disk_vs_dense": dms / ms,
                        "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20)))}
     return out
+
+
+def _timed(fn, flush, stream, n):
+    import torch
+    ts = []
+    for _ in range(n):
+        flush.fill_(3)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def gaussian_leg(d_img, flush, stream):
+    """Second workload on the same filter path: the 4K FP16 frame under a
+    tilt-shift sigma map (1..11 px), 11 fitted Gaussians with the paper's
+    L=6, T=8, against the dense spatially varying Gaussian (67 x 67 kernels,
+    41 LUT nodes) on the same frame."""
+    import torch
+
+    from paper_2512_04556_gb300 import disk
+    g = wl.G
+    H, W = g["H"], g["W"]
+    px = H * W
+    maps = wl.tilt_shift_map(H, W, *g["map_range"])[None]
+    d_maps = torch.from_numpy(maps).cuda()
+    b = disk.Basis.load(os.path.join(BASES, "gauss11_L6T8.dkb"))
+    tiles = disk.sv_filter_autotune(b, d_img, d_maps, stream=stream)
+    d_out = torch.empty_like(d_img)
+    ms = _timed(lambda: disk.sv_filter(b, d_img, d_maps, out=d_out, stream=stream), flush, stream, 10)
+    sig = np.linspace(1.0, 11.0, 41)
+    lut = torch.from_numpy(wl.gaussian_lut(sig, g["dense_K"])).cuda()
+    d_dense = torch.empty_like(d_img)
+    dms = _timed(lambda: disk.dense_sv([sig], lut, d_img, d_maps, out=d_dense, stream=stream),
+                 flush, stream, 3)
+    mse = float(((d_out.float() - d_dense.float()) ** 2).mean().item())
+    return {"value": px / (ms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": ms,
+            "L": b.L, "T": b.T, "nodes": "11 Gaussians, sigma 1..11 px",
+            "map": "tilt-shift, sigma 1..11", "tile": ", ".join(f"32x{8 * p}" for p in tiles),
+            "dense_ms": dms, "dense_kernel": f"{g['dense_K']}x{g['dense_K']}, 41 LUT nodes",
+            "speedup_disk_vs_dense": dms / ms,
+            "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20)))}
 
 
 # Relative MSE (sum (K_syn - K_tgt)^2 / sum K_tgt^2) that the plain fitter

@@ -5,6 +5,7 @@ quick checks): ``python -m paper_2512_04556_gb300.cases <name> [--reps N]``.
                 autotuned tiles as the benchmark uses)
   backward4k    full backward (image and basis gradients) on the same frame
   dense4k       dense spatially varying convolution on the same frame
+  gauss4k       4K RGB FP16 under a tilt-shift sigma map, 11 fitted Gaussians, L=6, T=8
   filter1080p   1080p RGB FP32, 16 fitted disks, L=4, T=16
   fit           64 uneven targets, L=4, T=16, 100 steps (sparse-sampling init)
   mlp           one training step of the learned initializer, batch 256
@@ -55,6 +56,14 @@ def main(argv=None):
             else:
                 go = torch.empty_like(di).uniform_(-1, 1)
                 run = lambda: disk.sv_filter_backward(b, di, go, dm)
+    elif a.name == "gauss4k":
+        g = wl.G
+        img = wl.to_fp16(wl.image_rects(g["H"], g["W"], 3))
+        maps = wl.tilt_shift_map(g["H"], g["W"], *g["map_range"])[None]
+        b = disk.Basis.load(os.path.join(BASES, "gauss11_L6T8.dkb"))
+        di, dm = torch.from_numpy(img).cuda(), torch.from_numpy(maps).cuda()
+        disk.sv_filter_autotune(b, di, dm)
+        run = lambda: disk.sv_filter(b, di, dm)
     elif a.name == "filter1080p":
         img = wl.image_rects(1080, 1920, 3)
         maps = wl.param_map(1080, 1920, 1.0, 32.0, sigma=96.0)[None]

@@ -167,6 +167,31 @@ def ellipse(radius: float, ratio: float, angle: float, K: int | None = None) -> 
     return _coverage((xr / a) ** 2 + (yr / b) ** 2 <= 1.0, K)
 
 
+def gaussian(sigma: float, K: int | None = None) -> np.ndarray:
+    """Isotropic Gaussian of standard deviation sigma px, 4 x 4 supersampled
+    over each pixel, unit sum, odd size 2 ceil(3 sigma) + 1."""
+    K = K or 2 * int(math.ceil(3.0 * sigma)) + 1
+    xx, yy = _grid(K)
+    g = np.exp(-(xx * xx + yy * yy) / (2.0 * sigma * sigma))
+    g = g.reshape(K, 4, K, 4).mean(axis=(1, 3))
+    return g / g.sum()
+
+
+def gaussian_lut(sigmas, K: int) -> np.ndarray:
+    return np.stack([gaussian(s, K) for s in sigmas]).astype(np.float32)
+
+
+def tilt_shift_map(H: int, W: int, lo: float, hi: float, focus: float = 0.55,
+                   band: float = 0.05, ramp: float = 0.4, seed: int = SEED_MAP) -> np.ndarray:
+    """Tilt-shift blur map: sharp (lo) inside a horizontal focus band around
+    row focus*H, rising linearly to hi over ramp*H, plus a faint smooth
+    perturbation; float32 [H][W]."""
+    y = np.arange(H)[:, None] / H
+    t = np.clip((np.abs(y - focus) - band) / ramp, 0.0, 1.0)
+    pert = 0.05 * (smooth_field(H, W, 96.0, seed, stream=7) - 0.5)
+    return np.clip(lo + (hi - lo) * (t + pert), lo, hi).astype(np.float32)
+
+
 def ellipse_params(radius: float, u: float) -> tuple[float, float, float]:
     """The 2-D kernel-space axis u in [0,1] couples anisotropy ratio 1+3u with
     rotation pi*u."""
@@ -249,6 +274,8 @@ C3 = dict(name="fit_batch_256", batch=256, L=4, T=16, steps=500, kmin=33, kmax=1
 C4 = dict(name="sv_4k_fp16_2d", H=2160, W=3840, C=3, L=4, T=24,
           nodes0=list(np.linspace(2.0, 40.0, 8)), nodes1=list(np.linspace(0.0, 1.0, 8)),
           map_range0=(2.0, 40.0), map_range1=(0.0, 1.0), map_sigma=192.0, dense_K=81)
+G = dict(name="sv_4k_fp16_gaussian_tilt_shift", H=2160, W=3840, C=3, L=6, T=8,
+         nodes=list(np.linspace(1.0, 11.0, 11)), map_range=(1.0, 11.0), dense_K=67)
 C5 = dict(name="mlp_init", train=50000, heldout=2000, L=4, T=16, hidden=512, depth=3, side=64)
 
 

@@ -10,10 +10,12 @@ half-widths, so that tap i means the same tap across nodes and blending them
 radial initialisation.
 
   bases/disk16_L4T16.dkb    16 disks, radius 1..32 px, L=4, T=16 (1-D)
+  bases/gauss11_L6T8.dkb    11 Gaussians, sigma 1..11 px, L=6, T=8 (1-D; the paper's
+                            6-layer, 8-sample configuration)
   bases/ellipse8x8_L4T24.dkb  8 x 8 ellipses, radius 2..40 px x u in [0,1]
                             (anisotropy 1+3u, rotation pi u), L=4, T=24 (2-D)
 
-Usage: python tests/golden/make_bases.py [--steps N]
+Usage: python tests/golden/make_bases.py [--steps N] [--only disk|ellipse|gauss]
 """
 import json
 import math
@@ -35,7 +37,12 @@ def _chain(args):
     from paper_2512_04556_gb300 import workloads as wl
     thetas, losses, prev = [], [], None
     for r in radii:
-        tgt = wl.disk(r) if kind == "disk" else wl.ellipse(*wl.ellipse_params(r, u))
+        if kind == "disk":
+            tgt = wl.disk(r)
+        elif kind == "gauss":
+            tgt = wl.gaussian(r)
+        else:
+            tgt = wl.ellipse(*wl.ellipse_params(r, u))
         K = tgt.shape[0]
         hw = max(1.0, (K - 1) / 2)
         if prev is None:
@@ -53,40 +60,54 @@ def _chain(args):
     return kind, u, thetas, losses
 
 
-def main(steps=1000):
+def main(steps=1000, only=None):
     sys.path.insert(0, ROOT)
     import numpy as np
     from oracle import basis_io
     from paper_2512_04556_gb300 import workloads as wl
     os.makedirs(OUT, exist_ok=True)
     c2, c4 = wl.C2, wl.C4
+    g = wl.G
     jobs = [("disk", list(c2["nodes"]), 0.0, c2["L"], c2["T"], steps)]
     jobs += [("ellipse", list(c4["nodes0"]), float(u), c4["L"], c4["T"], steps) for u in c4["nodes1"]]
+    jobs += [("gauss", list(g["nodes"]), 0.0, g["L"], g["T"], steps)]
+    if only:
+        jobs = [j for j in jobs if j[0] == only]
     os.environ["OMP_NUM_THREADS"] = "1"
     t0 = time.time()
     with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 4)) as pool:
         res = pool.map(_chain, jobs)
-    report = {"steps": steps, "seconds": time.time() - t0}
-    disk_th = [r for r in res if r[0] == "disk"][0]
-    basis_io.write(os.path.join(OUT, "disk16_L4T16.dkb"), [c2["nodes"]], np.stack(disk_th[2]))
-    report["disk"] = disk_th[3]
-    ell = {r[1]: r for r in res if r[0] == "ellipse"}
-    th = np.zeros((8, 8, c4["L"], c4["T"], 3))
-    losses = []
-    for b, u in enumerate(c4["nodes1"]):
-        for a in range(8):
-            th[a, b] = ell[float(u)][2][a]
-        losses += ell[float(u)][3]
-    basis_io.write(os.path.join(OUT, "ellipse8x8_L4T24.dkb"), [c4["nodes0"], c4["nodes1"]],
-                   th.reshape(64, c4["L"], c4["T"], 3))
-    report["ellipse"] = losses
-    with open(os.path.join(OUT, "fit_report.json"), "w") as f:
+    rpath = os.path.join(OUT, "fit_report.json")
+    report = json.load(open(rpath)) if os.path.exists(rpath) else {}
+    report["steps"] = steps
+    kinds = {r[0] for r in res}
+    if "disk" in kinds:
+        disk_th = [r for r in res if r[0] == "disk"][0]
+        basis_io.write(os.path.join(OUT, "disk16_L4T16.dkb"), [c2["nodes"]], np.stack(disk_th[2]))
+        report["disk"] = disk_th[3]
+    if "gauss" in kinds:
+        gth = [r for r in res if r[0] == "gauss"][0]
+        basis_io.write(os.path.join(OUT, "gauss11_L6T8.dkb"), [g["nodes"]], np.stack(gth[2]))
+        report["gauss"] = gth[3]
+    if "ellipse" in kinds:
+        ell = {r[1]: r for r in res if r[0] == "ellipse"}
+        th = np.zeros((8, 8, c4["L"], c4["T"], 3))
+        losses = []
+        for b, u in enumerate(c4["nodes1"]):
+            for a in range(8):
+                th[a, b] = ell[float(u)][2][a]
+            losses += ell[float(u)][3]
+        basis_io.write(os.path.join(OUT, "ellipse8x8_L4T24.dkb"), [c4["nodes0"], c4["nodes1"]],
+                       th.reshape(64, c4["L"], c4["T"], 3))
+        report["ellipse"] = losses
+    with open(rpath, "w") as f:
         json.dump(report, f, indent=1)
-    print(f"wrote bases in {report['seconds']:.0f} s")
+    print(f"wrote bases in {time.time() - t0:.0f} s")
 
 
 if __name__ == "__main__":
     n = 1000
     if "--steps" in sys.argv:
         n = int(sys.argv[sys.argv.index("--steps") + 1])
-    main(n)
+    only = sys.argv[sys.argv.index("--only") + 1] if "--only" in sys.argv else None
+    main(n, only)

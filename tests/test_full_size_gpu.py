@@ -101,6 +101,34 @@ def test_4k_fp16_2d_image_gradient_sampled(torch_cuda):
     assert np.abs(got - want).max() / np.abs(want).max() <= 1e-5
 
 
+def test_4k_fp16_gaussian_tilt_shift_sampled(torch_cuda):
+    """3840 x 2160 FP16 under a tilt-shift sigma map (1..11 px), 11 fitted
+    Gaussians, L=6, T=8, autotuned tiles as the benchmark's Gaussian leg."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    g = wl.G
+    H, W = g["H"], g["W"]
+    img = wl.to_fp16(wl.image_rects(H, W, 3))
+    maps = wl.tilt_shift_map(H, W, *g["map_range"])[None]
+    path = os.path.join(BASES, "gauss11_L6T8.dkb")
+    b = disk.Basis.load(path)
+    di, dm = torch.from_numpy(img).cuda(), torch.from_numpy(maps).cuda()
+    disk.sv_filter_autotune(b, di, dm)
+    out = disk.sv_filter(b, di, dm).cpu().numpy()
+    axes, th = basis_io.read(path)
+    th = th.astype(np.float64)
+    R = _cone(th)
+    fn = lambda a, m: oracle.sv_filter(a, m, [len(axes[0])], axes[0].astype(np.float64), th)
+    pts = _samples(H, W, 20, 3)
+    pts += [(int(0.55 * H), 100), (int(0.55 * H) + 120, 2000)]      # in and at the edge of focus
+    got, want = [], []
+    for (y, x) in pts:
+        want.append(np.float16(_crop_oracle(fn, img, maps, y, x, R)).astype(np.float64))
+        got.append(out[y, x].astype(np.float64))
+    got, want = np.array(got), np.array(want)
+    assert np.abs(got - want).max() / np.abs(want).max() <= 2e-3
+
+
 def test_1080p_fp32_1d_filter_sampled(torch_cuda):
     """1920 x 1080 FP32, 16 fitted disks (radius 1..32), L=4, T=16."""
     torch = torch_cuda
