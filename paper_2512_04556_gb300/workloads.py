@@ -261,6 +261,20 @@ def shape_batch(n: int, seed: int = SEED_SHAPE, kmin: int = 33, kmax: int = 129,
     return out
 
 
+def ring_batch(n: int, seed: int = SEED_SHAPE, kmin: int = 33, kmax: int = 81,
+               first: int = 0) -> list[np.ndarray]:
+    """n seeded ring kernels (the layer/sample ablation's target family):
+    odd size uniform over {kmin..kmax}, outer radius 0.6..1.0 of the
+    half-width, width 0.06..0.25 of the radius (at least 1.5 px)."""
+    out = []
+    for j in range(first, first + n):
+        g = rng(seed, 50000 + j)
+        K = int(g.integers(kmin // 2, kmax // 2 + 1)) * 2 + 1
+        r = g.uniform(0.6, 1.0) * ((K - 1) / 2.0 - 0.5)
+        out.append(ring(r, max(1.5, g.uniform(0.06, 0.25) * r), K))
+    return out
+
+
 # --------------------------------------------------------------------------
 # The five workload presets (sizes and node sets of the benchmark configs)
 # --------------------------------------------------------------------------
