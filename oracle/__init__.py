@@ -58,6 +58,9 @@ def lib():
                        _ip, _dp, ctypes.c_int, ctypes.c_int, _dp, _dp]
             l.orc_sv_filter.argtypes = sv_args
             l.orc_sv_filter_adjoint.argtypes = sv_args
+            l.orc_sv_filter_rot.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                            ctypes.c_int, _ip, _dp, ctypes.c_int, ctypes.c_int,
+                                            _dp, _dp]
             l.orc_sv_filter_grad_theta.argtypes = [_dp, _dp, ctypes.c_int, ctypes.c_int,
                                                    ctypes.c_int, _dp, ctypes.c_int, _ip, _dp,
                                                    ctypes.c_int, ctypes.c_int, _dp, _dp]
@@ -157,6 +160,23 @@ def sv_filter(img, maps, n_nodes, node_vals, theta) -> np.ndarray:
                              out.ctypes.data_as(_dp))
     if rc:
         raise ValueError(f"orc_sv_filter failed ({rc})")
+    return out
+
+
+def sv_filter_rotated(img, maps, angle, n_nodes, node_vals, theta) -> np.ndarray:
+    """sv_filter with every pixel's blended tap offsets rotated by angle[H][W]
+    (radians, x right, y down): (dx, dy) -> (dx cos a - dy sin a, dx sin a + dy cos a)."""
+    img, ip = _d(img)
+    H, W, C = img.shape
+    maps, mp = _d(np.reshape(maps, (-1, H, W)))
+    ang, ap = _d(np.reshape(angle, (H, W)))
+    nn, nnp, nv, nvp, th, thp = _basis_args(n_nodes, node_vals, theta)
+    B, L, T, _ = th.shape
+    out = np.zeros_like(img)
+    rc = lib().orc_sv_filter_rot(ip, H, W, C, mp, ap, len(nn), nnp, nvp, L, T, thp,
+                                 out.ctypes.data_as(_dp))
+    if rc:
+        raise ValueError(f"orc_sv_filter_rot failed ({rc})")
     return out
 
 

@@ -9,7 +9,7 @@
  *
  * Every routine is the paper's definition written out in FP64 with no blocking,
  * fusion or reordering beyond what the definition states.  Where the paper is
- * silent, the reading taken is stated at the routine and collected in the design doc.
+ * silent, the reading taken is stated at the routine.
  *
  * Conventions (shared by name, not by code, with the library):
  *   image      double [H][W][C] row-major, pixel (v,u) = (row, column)
@@ -211,6 +211,47 @@ int orc_sv_filter(const double *img, int H, int W, int C, const double *maps,
   memcpy(a, img, sizeof(double) * n);
   for (int l = 0; l < L; l++) {
     sv_layer_taps(maps, H, W, dims, n_nodes, node_vals, L, T, theta, l, taps);
+    orc_layer(a, b, H, W, C, T, taps, (long)T * 3, 0);
+    double *s = a; a = b; b = s;
+  }
+  memcpy(out, a, sizeof(double) * n);
+  free(a); free(b); free(taps);
+  return ORC_OK;
+}
+
+/* Spatially varying filter with a per-pixel rotation of the complex: as
+ * orc_sv_filter, but after the Eq. 9 blend every tap offset of pixel x is
+ * rotated by angle[x] (radians; x right, y down):
+ *   (dx, dy) -> (dx cos a - dy sin a, dx sin a + dy cos a).
+ * Rotating every offset of every layer rotates the impulse response (Eq. 10)
+ * of a shift-invariant complex by the same angle, which is how the 2-D
+ * effects of Sec. 5.3 (rotational and radial blur: strength and local blur
+ * angle) reduce to a basis over strength alone.  A non-finite angle acts as
+ * zero. */
+int orc_sv_filter_rot(const double *img, int H, int W, int C, const double *maps,
+                      const double *angle, int dims, const int *n_nodes,
+                      const double *node_vals, int L, int T, const double *theta,
+                      double *out) {
+  if (H <= 0 || W <= 0 || C <= 0 || L <= 0 || T <= 0 || (dims != 1 && dims != 2))
+    return ORC_EINVAL;
+  long n = (long)H * W * C, HW = (long)H * W;
+  double *a = (double *)malloc(sizeof(double) * n);
+  double *b = (double *)malloc(sizeof(double) * n);
+  double *taps = (double *)malloc(sizeof(double) * HW * T * 3);
+  if (!a || !b || !taps) { free(a); free(b); free(taps); return ORC_ENOMEM; }
+  memcpy(a, img, sizeof(double) * n);
+  for (int l = 0; l < L; l++) {
+    sv_layer_taps(maps, H, W, dims, n_nodes, node_vals, L, T, theta, l, taps);
+    for (long px = 0; px < HW; px++) {
+      double phi = isfinite(angle[px]) ? angle[px] : 0.0;
+      double cs = cos(phi), sn = sin(phi);
+      for (int i = 0; i < T; i++) {
+        double *t = taps + (px * T + i) * 3;
+        double dx = t[0], dy = t[1];
+        t[0] = dx * cs - dy * sn;
+        t[1] = dx * sn + dy * cs;
+      }
+    }
     orc_layer(a, b, H, W, C, T, taps, (long)T * 3, 0);
     double *s = a; a = b; b = s;
   }
