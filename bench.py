@@ -271,6 +271,8 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
     mse = float(((o - dd) ** 2).mean().item())
     out["fit"] = fit_leg(stream)
     out["gaussian_tilt_shift"] = gaussian_leg(d_img, flush, stream)
+    out["radial_motion"] = rotated_leg(wl.RM, "line12_L3T8.dkb", False, d_img, flush, stream)
+    out["rotational_bokeh"] = rotated_leg(wl.RB, "cateye12_L4T16.dkb", True, d_img, flush, stream)
     out["dense_sv"] = {"value": px / (dms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": dms,
                        "kernel_max": "81x81", "lut": "16x16 ellipse grid",
                        "speedup_disk_vs_dense": dms / ms,
@@ -333,6 +335,45 @@ def gaussian_leg(d_img, flush, stream):
             "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20))),
             "basis_fit_on_gpu": {"ms": fms, "targets": len(sizes), "steps": 1000,
                                  "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse_g, 1e-20)))}}
+
+
+def rotated_leg(preset, basis_file, tangential, d_img, flush, stream):
+    """The 2-D effects driven by strength and local angle, as a 1-D basis over
+    strength turned per pixel at run time: radial motion blur (segments along
+    the direction to the frame centre) or rotational bokeh (aspect-2 ellipses
+    across it), on the 4K FP16 frame, against the dense spatially varying
+    convolution whose node kernels are the targets on a (strength, angle mod pi)
+    grid."""
+    import torch
+
+    from paper_2512_04556_gb300 import disk
+    H, W = preset["H"], preset["W"]
+    px = H * W
+    strength, angle = wl.radial_maps(H, W, *preset["map_range"], tangential=tangential)
+    d_s = torch.from_numpy(strength[None]).cuda()
+    d_a = torch.from_numpy(angle).cuda()
+    b = disk.Basis.load(os.path.join(BASES, basis_file))
+    tiles = disk.sv_filter_rotated_autotune(b, d_img, d_s, d_a, stream=stream)
+    d_out = torch.empty_like(d_img)
+    ms = _timed(lambda: disk.sv_filter_rotated(b, d_img, d_s, d_a, out=d_out, stream=stream),
+                flush, stream, 10)
+    s_nodes = np.linspace(*preset["map_range"], 16)
+    a_nodes = np.linspace(0.0, np.pi, preset["dense_angles"])
+    K = preset["dense_K"]
+    shape = wl.line if not tangential else wl.cat_eye
+    lut = torch.from_numpy(np.stack([shape(s, K, angle=a) for s in s_nodes for a in a_nodes])
+                           .astype(np.float32)).cuda()
+    d_m2 = torch.from_numpy(np.stack([strength, np.mod(angle, np.pi).astype(np.float32)])).cuda()
+    d_dense = torch.empty_like(d_img)
+    dms = _timed(lambda: disk.dense_sv([s_nodes, a_nodes], lut, d_img, d_m2, out=d_dense,
+                                       stream=stream), flush, stream, 3)
+    mse = float(((d_out.float() - d_dense.float()) ** 2).mean().item())
+    return {"value": px / (ms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": ms,
+            "L": b.L, "T": b.T, "nodes": f"{b.n_nodes[0]} along the strength axis, turned per pixel",
+            "tile": ", ".join(f"32x{8 * p}" for p in tiles),
+            "dense_ms": dms, "dense_kernel": f"{K}x{K}, 16 strengths x {len(a_nodes)} angles",
+            "speedup_disk_vs_dense": dms / ms,
+            "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20)))}
 
 
 # Relative MSE (sum (K_syn - K_tgt)^2 / sum K_tgt^2) that the plain fitter
@@ -477,7 +518,8 @@ def main():
     if rank == 0:
         line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"],
                     clocks=res["clocks"], gpu_launches=res["gpu_launches"])
-        for k in ("roofline", "e2e", "dense_sv", "backward_image", "fit", "gaussian_tilt_shift", "smem_model"):
+        for k in ("roofline", "e2e", "dense_sv", "backward_image", "fit", "gaussian_tilt_shift",
+                  "radial_motion", "rotational_bokeh", "smem_model"):
             if k in res:
                 line[k] = res[k]
         line["config"]["tile"] = res["tile"]

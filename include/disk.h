@@ -202,6 +202,31 @@ int disk_sv_filter_autotune(const disk_basis *basis, const void *d_in, size_t in
                             void *d_out, size_t out_pitch, int H, int W, int C,
                             int dtype, const float *d_maps, int *chosen, void *stream);
 
+/* Spatially varying filter with a per-pixel rotation of the complex
+ * (Sec. 5.3: the rotational-bokeh and radial-motion effects are driven by a
+ * blur strength and a local blur angle).  Computes what disk_sv_filter
+ * computes, except that after the Eq. 9 blend every tap offset of output
+ * pixel x is turned by angle[x] (radians; x to the right, y down):
+ *   (dx, dy) -> (dx cos a - dy sin a, dx sin a + dy cos a).
+ * Turning every offset of every layer turns the impulse response (Eq. 10) of
+ * a shift-invariant complex by the same angle, so a basis over blur strength
+ * (and, for 2-D bases, shape) plus an angle map replaces a basis grid over
+ * the angle.  d_angle: float32 [H][W], device, caller-owned; a non-finite
+ * angle acts as 0.  Other arguments as disk_sv_filter.  The shared-memory
+ * halo of layer l comes from its largest Euclidean tap length (a turned tap
+ * keeps its length); DISK_ERR_UNSUPPORTED if that halo does not fit.
+ * Tile choice: recorded by disk_sv_filter_rotated_autotune (separately from
+ * the plain filter's), else 32 x 16. */
+int disk_sv_filter_rotated(const disk_basis *basis, const void *d_in, size_t in_pitch,
+                           void *d_out, size_t out_pitch, int H, int W, int C, int dtype,
+                           const float *d_maps, const float *d_angle, void *stream);
+
+/* Tile autotuner of disk_sv_filter_rotated (as disk_sv_filter_autotune). */
+int disk_sv_filter_rotated_autotune(const disk_basis *basis, const void *d_in,
+                                    size_t in_pitch, void *d_out, size_t out_pitch, int H,
+                                    int W, int C, int dtype, const float *d_maps,
+                                    const float *d_angle, int *chosen, void *stream);
+
 /* Records one tile configuration (pixels per thread: 2 or 4) for every
  * layer, for this (H, W, C, dtype), in the basis handle. */
 int disk_sv_filter_set_tile(const disk_basis *basis, int H, int W, int C, int dtype,

@@ -6,6 +6,8 @@ quick checks): ``python -m paper_2512_04556_gb300.cases <name> [--reps N]``.
   backward4k    full backward (image and basis gradients) on the same frame
   dense4k       dense spatially varying convolution on the same frame
   gauss4k       4K RGB FP16 under a tilt-shift sigma map, 11 fitted Gaussians, L=6, T=8
+  radial4k      4K RGB FP16 radial motion blur: 12 fitted segments (L=3, T=8) turned per pixel
+  bokeh4k       4K RGB FP16 rotational bokeh: 12 fitted aspect-2 ellipses (L=4, T=16) turned
   filter1080p   1080p RGB FP32, 16 fitted disks, L=4, T=16
   fit           64 uneven targets, L=4, T=16, 100 steps (sparse-sampling init)
   mlp           one training step of the learned initializer, batch 256
@@ -64,6 +66,15 @@ def main(argv=None):
         di, dm = torch.from_numpy(img).cuda(), torch.from_numpy(maps).cuda()
         disk.sv_filter_autotune(b, di, dm)
         run = lambda: disk.sv_filter(b, di, dm)
+    elif a.name in ("radial4k", "bokeh4k"):
+        pre, fname = (wl.RM, "line12_L3T8.dkb") if a.name == "radial4k" else (wl.RB, "cateye12_L4T16.dkb")
+        img = wl.to_fp16(wl.image_rects(pre["H"], pre["W"], 3))
+        st, ang = wl.radial_maps(pre["H"], pre["W"], *pre["map_range"], tangential=a.name == "bokeh4k")
+        b = disk.Basis.load(os.path.join(BASES, fname))
+        di, dm, da = (torch.from_numpy(img).cuda(), torch.from_numpy(st[None]).cuda(),
+                      torch.from_numpy(ang).cuda())
+        disk.sv_filter_rotated_autotune(b, di, dm, da)
+        run = lambda: disk.sv_filter_rotated(b, di, dm, da)
     elif a.name == "filter1080p":
         img = wl.image_rects(1080, 1920, 3)
         maps = wl.param_map(1080, 1920, 1.0, 32.0, sigma=96.0)[None]

@@ -115,6 +115,7 @@ extern "C" int disk_basis_from_arrays(int dims, const int *n_nodes, const float 
   size_t n = (size_t)b->B * L * T * 3;
   b->theta.assign(theta, theta + n);
   b->reach.assign(L, 0.f);
+  b->reach_norm.assign(L, 0.f);
   std::vector<float4> taps((size_t)L * b->B * T);
   for (int k = 0; k < b->B; ++k)
     for (int l = 0; l < L; ++l)
@@ -126,6 +127,7 @@ extern "C" int disk_basis_from_arrays(int dims, const int *n_nodes, const float 
         if (r > DISK_MAX_REACH)
           return fail(DISK_ERR_UNSUPPORTED, "tap offset beyond DISK_MAX_REACH");
         b->reach[l] = std::fmax(b->reach[l], r);
+        b->reach_norm[l] = std::fmax(b->reach_norm[l], std::hypot(t[0], t[1]));
         taps[((size_t)l * b->B + k) * T + i] = make_float4(t[0], t[1], t[2], t[2]);
       }
   DISK_TRY_CUDA(cudaGetDevice(&b->device), "cudaGetDevice");

@@ -20,10 +20,12 @@ struct disk_basis {
   std::vector<float> node_vals;  // n_nodes[0] (+ n_nodes[1]) values
   std::vector<float> theta;      // [B][L][T][3] = (dx, dy, w), pixels
   std::vector<float> reach;      // [L]: max over nodes, taps of max(|dx|,|dy|)
+  std::vector<float> reach_norm; // [L]: max over nodes, taps of sqrt(dx^2 + dy^2)
   int device = 0;
   float4 *d_taps = nullptr;      // [L][B][T] = (dx, dy, w, w)
   // filter tile configuration (pixels per thread) of every layer, chosen by
-  // disk_sv_filter_autotune per (H, W, C, dtype); read by disk_sv_filter
+  // disk_sv_filter_autotune per (H, W, C, dtype | rotated << 8); read by
+  // disk_sv_filter and disk_sv_filter_rotated
   mutable std::mutex tune_mu;
   mutable std::map<std::tuple<int, int, int, int>, std::vector<int>> tune_pix;
 };
@@ -39,6 +41,12 @@ inline int halo_of(float reach) {
   // Offsets with |o| <= reach touch pixels within ceil(reach) + 1 of the
   // output pixel (the +1 is the bilinear footprint).
   return static_cast<int>(__builtin_ceilf(reach)) + 1;
+}
+
+// Reach of layer l: per-axis for the plain filter; the Euclidean tap length
+// when offsets are rotated at run time (a turned tap keeps its length).
+inline float layer_reach(const disk_basis *b, int l, bool rotated) {
+  return rotated ? b->reach_norm[l] : b->reach[l];
 }
 
 // Kernel-space axis as the kernels see it: node values and inverse spacings.

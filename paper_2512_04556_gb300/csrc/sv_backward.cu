@@ -391,6 +391,7 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
                           cudaStream_t s) {
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
+  P.angle = nullptr;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16, mid = intermediate_kind(dtype);
@@ -409,8 +410,8 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
           const float *t = &b->theta[(((size_t)k * b->L + l) * b->T + i) * 3];
           P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
         }
-    const int rc = b->dims == 1 ? launch_sv_layer<1, NP>(l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix)
-                                : launch_sv_layer<2, NP>(l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix);
+    const int rc = b->dims == 1 ? launch_sv_layer<1, NP, false>(l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix)
+                                : launch_sv_layer<2, NP, false>(l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix);
     if (rc) return rc;
   }
   return DISK_OK;

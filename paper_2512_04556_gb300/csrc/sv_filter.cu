@@ -1,6 +1,7 @@
 // disk_sv_filter: the spatially varying cascade (Sec. 4.3 Eq. 9 + Sec. 3.2
 // Eq. 3) as one shared-memory-staged launch per layer (kernel in
-// sv_layer.cuh).  Intermediate layers live in RGBA planes of the image's
+// sv_layer.cuh); disk_sv_filter_rotated: the same with every pixel's taps
+// turned by a per-pixel angle (Sec. 5.3's rotational and radial blur).  Intermediate layers live in RGBA planes of the image's
 // storage precision (FP32 or FP16) taken from the stream-ordered pool; the
 // first layer reads the caller's image and the last writes the caller's
 // output.
@@ -12,10 +13,11 @@ namespace {
 template <int NP>
 int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
-               cudaStream_t s, const int *pix, cudaEvent_t *ev) {
+               const float *d_angle, cudaStream_t s, const int *pix, cudaEvent_t *ev) {
   // The parameter block is large; keep it off the host stack.
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
+  P.angle = d_angle;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
@@ -34,7 +36,7 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   }
   int rc = DISK_OK;
   for (int l = 0; l < L && rc == DISK_OK; ++l) {
-    P.halo = halo_of(b->reach[l]);
+    P.halo = halo_of(layer_reach(b, l, d_angle != nullptr));
     P.region_w = kSvTileW + 2 * P.halo;
     const int src = l == 0 ? user : mid;
     const int dst = l == L - 1 ? user : mid;
@@ -53,16 +55,20 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
         }
     }
     if (ev) cudaEventRecord(ev[l], s);
-    rc = b->dims == 1 ? launch_sv_layer<1, NP>(src, dst, C, P, s, pix[l])
-                      : launch_sv_layer<2, NP>(src, dst, C, P, s, pix[l]);
+    if (d_angle)
+      rc = b->dims == 1 ? launch_sv_layer<1, NP, true>(src, dst, C, P, s, pix[l])
+                        : launch_sv_layer<2, NP, true>(src, dst, C, P, s, pix[l]);
+    else
+      rc = b->dims == 1 ? launch_sv_layer<1, NP, false>(src, dst, C, P, s, pix[l])
+                        : launch_sv_layer<2, NP, false>(src, dst, C, P, s, pix[l]);
   }
   if (ev && rc == DISK_OK) cudaEventRecord(ev[L], s);
   for (int i = 0; i < nbuf; ++i) cudaFreeAsync(bufs[i], s);
   return rc;
 }
 
-bool fits_layer(const disk_basis *b, int C, int l, int pix) {
-  const int h = halo_of(b->reach[l]);
+bool fits_layer(const disk_basis *b, int C, int l, int pix, bool rot) {
+  const int h = halo_of(layer_reach(b, l, rot));
   const size_t smem = (size_t)(kSvTileW + 2 * h) * (sv_tile_h(pix) + 2 * h) * sv_stage_bytes(C);
   return smem <= (size_t)kSvMaxSmem;
 }
@@ -70,20 +76,26 @@ bool fits_layer(const disk_basis *b, int C, int l, int pix) {
 // Per-layer tile configuration for this frame shape: the recorded one, or
 // the default, with any layer whose halo does not fit falling back to the
 // smaller tile.
-std::vector<int> layer_pix(const disk_basis *b, int H, int W, int C, int dtype) {
+// Tuning key: the frame shape, the storage type and the variant.
+std::tuple<int, int, int, int> tune_key(int H, int W, int C, int dtype, bool rot) {
+  return std::make_tuple(H, W, C, dtype | (rot ? 0x100 : 0));
+}
+
+std::vector<int> layer_pix(const disk_basis *b, int H, int W, int C, int dtype, bool rot) {
   std::vector<int> pix(b->L, kSvDefaultPix);
   {
     std::lock_guard<std::mutex> lock(b->tune_mu);
-    auto it = b->tune_pix.find(std::make_tuple(H, W, C, dtype));
+    auto it = b->tune_pix.find(tune_key(H, W, C, dtype, rot));
     if (it != b->tune_pix.end() && (int)it->second.size() == b->L) pix = it->second;
   }
   for (int l = 0; l < b->L; ++l)
-    if (!fits_layer(b, C, l, pix[l])) pix[l] = 2;
+    if (!fits_layer(b, C, l, pix[l], rot)) pix[l] = 2;
   return pix;
 }
 
 int check_filter_args(const disk_basis *b, const void *d_in, size_t in_pitch, const void *d_out,
-                      size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps) {
+                      size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
+                      bool rot = false) {
   if (!b) return fail(DISK_ERR_INVALID_ARG, "null basis");
   int rc = validate_image_args(d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps);
   if (rc) return rc;
@@ -91,53 +103,43 @@ int check_filter_args(const disk_basis *b, const void *d_in, size_t in_pitch, co
   DISK_TRY_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
   for (int l = 0; l < b->L; ++l)
-    if (!fits_layer(b, C, l, 2)) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
+    if (!fits_layer(b, C, l, 2, rot))
+      return fail(DISK_ERR_UNSUPPORTED, rot ? "layer halo (rotated: Euclidean tap length) exceeds shared memory"
+                                            : "layer halo exceeds shared memory");
   return DISK_OK;
 }
 
 int filter_with(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                 size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
-                cudaStream_t s, const int *pix, cudaEvent_t *ev = nullptr) {
+                const float *d_angle, cudaStream_t s, const int *pix, cudaEvent_t *ev = nullptr) {
   if ((size_t)b->B * b->T <= (size_t)kSvParamTaps)
-    return run_filter<kSvParamTaps>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix, ev);
-  return run_filter<0>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix, ev);
+    return run_filter<kSvParamTaps>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps,
+                                    d_angle, s, pix, ev);
+  return run_filter<0>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, d_angle, s,
+                       pix, ev);
 }
 
-}  // namespace
-}  // namespace disk
-
-using namespace disk;
-
-extern "C" int disk_sv_filter(const disk_basis *b, const void *d_in, size_t in_pitch,
-                              void *d_out, size_t out_pitch, int H, int W, int C, int dtype,
-                              const float *d_maps, void *stream) {
-  int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps);
-  if (rc) return rc;
-  const std::vector<int> pix = layer_pix(b, H, W, C, dtype);
-  return filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps,
-                     static_cast<cudaStream_t>(stream), pix.data());
-}
-
-extern "C" int disk_sv_filter_autotune(const disk_basis *b, const void *d_in, size_t in_pitch,
-                                       void *d_out, size_t out_pitch, int H, int W, int C,
-                                       int dtype, const float *d_maps, int *chosen,
-                                       void *stream) {
-  int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps);
-  if (rc) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// Times both tile configurations layer by layer (CUDA events, three passes
+// each after a warm-up pass) and records the faster one per layer.
+int autotune(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
+             size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
+             const float *d_angle, int *chosen, cudaStream_t s) {
+  const bool rot = d_angle != nullptr;
   const int L = b->L;
   std::vector<cudaEvent_t> ev(L + 1);
   for (auto &e : ev) DISK_TRY_CUDA(cudaEventCreate(&e), "cudaEventCreate");
   const int cand[2] = {2, 4};
   std::vector<float> best_ms(L, 1e30f);
   std::vector<int> best(L, 2);
+  int rc = DISK_OK;
   for (int c = 0; c < 2 && rc == DISK_OK; ++c) {
     std::vector<int> pix(L);
-    for (int l = 0; l < L; ++l) pix[l] = fits_layer(b, C, l, cand[c]) ? cand[c] : 2;
-    rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix.data());
+    for (int l = 0; l < L; ++l) pix[l] = fits_layer(b, C, l, cand[c], rot) ? cand[c] : 2;
+    rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, d_angle, s,
+                     pix.data());
     for (int r = 0; r < 3 && rc == DISK_OK; ++r) {
-      rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, s, pix.data(),
-                       ev.data());
+      rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, d_angle, s,
+                       pix.data(), ev.data());
       cudaError_t e = cudaEventSynchronize(ev[L]);
       if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
       for (int l = 0; l < L; ++l) {
@@ -152,19 +154,68 @@ extern "C" int disk_sv_filter_autotune(const disk_basis *b, const void *d_in, si
   if (rc) return rc;
   {
     std::lock_guard<std::mutex> lock(b->tune_mu);
-    b->tune_pix[std::make_tuple(H, W, C, dtype)] = best;
+    b->tune_pix[tune_key(H, W, C, dtype, rot)] = best;
   }
   if (chosen) for (int l = 0; l < L; ++l) chosen[l] = best[l];
   return DISK_OK;
+}
+
+}  // namespace
+}  // namespace disk
+
+using namespace disk;
+
+extern "C" int disk_sv_filter(const disk_basis *b, const void *d_in, size_t in_pitch,
+                              void *d_out, size_t out_pitch, int H, int W, int C, int dtype,
+                              const float *d_maps, void *stream) {
+  int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps);
+  if (rc) return rc;
+  const std::vector<int> pix = layer_pix(b, H, W, C, dtype, false);
+  return filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, nullptr,
+                     static_cast<cudaStream_t>(stream), pix.data());
+}
+
+extern "C" int disk_sv_filter_autotune(const disk_basis *b, const void *d_in, size_t in_pitch,
+                                       void *d_out, size_t out_pitch, int H, int W, int C,
+                                       int dtype, const float *d_maps, int *chosen,
+                                       void *stream) {
+  int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps);
+  if (rc) return rc;
+  return autotune(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, nullptr, chosen,
+                  static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int disk_sv_filter_rotated(const disk_basis *b, const void *d_in, size_t in_pitch,
+                                      void *d_out, size_t out_pitch, int H, int W, int C,
+                                      int dtype, const float *d_maps, const float *d_angle,
+                                      void *stream) {
+  if (!d_angle) return fail(DISK_ERR_INVALID_ARG, "null angle map");
+  int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, true);
+  if (rc) return rc;
+  const std::vector<int> pix = layer_pix(b, H, W, C, dtype, true);
+  return filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, d_angle,
+                     static_cast<cudaStream_t>(stream), pix.data());
+}
+
+extern "C" int disk_sv_filter_rotated_autotune(const disk_basis *b, const void *d_in,
+                                               size_t in_pitch, void *d_out, size_t out_pitch,
+                                               int H, int W, int C, int dtype,
+                                               const float *d_maps, const float *d_angle,
+                                               int *chosen, void *stream) {
+  if (!d_angle) return fail(DISK_ERR_INVALID_ARG, "null angle map");
+  int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, true);
+  if (rc) return rc;
+  return autotune(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, d_angle, chosen,
+                  static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int disk_sv_filter_set_tile(const disk_basis *b, int H, int W, int C, int dtype, int pix) {
   if (!b) return fail(DISK_ERR_INVALID_ARG, "null basis");
   if (pix != 2 && pix != 4) return fail(DISK_ERR_INVALID_ARG, "pixels per thread must be 2 or 4");
   for (int l = 0; l < b->L; ++l)
-    if (!fits_layer(b, C, l, pix))
+    if (!fits_layer(b, C, l, pix, false))
       return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory for this tile");
   std::lock_guard<std::mutex> lock(b->tune_mu);
-  b->tune_pix[std::make_tuple(H, W, C, dtype)] = std::vector<int>(b->L, pix);
+  b->tune_pix[tune_key(H, W, C, dtype, false)] = std::vector<int>(b->L, pix);
   return DISK_OK;
 }

@@ -43,6 +43,7 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
                 float4 *planes, cudaStream_t s) {
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
+  P.angle = nullptr;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
@@ -71,8 +72,8 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
           P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
         }
     }
-    rc = b->dims == 1 ? launch_sv_layer<1, NP>(src, dst, C, P, s, kSvDefaultPix)
-                      : launch_sv_layer<2, NP>(src, dst, C, P, s, kSvDefaultPix);
+    rc = b->dims == 1 ? launch_sv_layer<1, NP, false>(src, dst, C, P, s, kSvDefaultPix)
+                      : launch_sv_layer<2, NP, false>(src, dst, C, P, s, kSvDefaultPix);
   }
   return rc;
 }

@@ -40,6 +40,7 @@ struct SvLayerParams {
   void *dst;
   long long dst_pitch;
   const float *maps;
+  const float *angle;   // [H][W] radians, rotated variant only
   const float4 *gtaps;  // [B][T] of this layer when NP == 0: (dx, dy, w, w)
   int H, W, C, T, halo, region_w;
   AxisNodes ax[2];
@@ -92,14 +93,20 @@ __device__ __forceinline__ void add_corner(const Staged &st, int e, const float2
   }
 }
 
+// Rotation of a pixel's offsets as two pairs: (cos, sin) and (-sin, cos).
+struct RotPairs {
+  float2 c, s;
+};
+
 // One tap of one pixel: the Eq. 9 blend of the node taps (dx, dy, w, w) with
-// the pixel's weights, the integer/fraction split of the offset, and the
-// Eq. 2 bilinear sample from the staged region, all in packed FP32 pairs:
-// (dx, dy) and the corner weights travel as pairs, colour as (r, g) + b.
-template <int DIMS, int CH>
+// the pixel's weights, the optional rotation of the blended offset, the
+// integer/fraction split of the offset, and the Eq. 2 bilinear sample from
+// the staged region, all in packed FP32 pairs: (dx, dy) and the corner
+// weights travel as pairs, colour as (r, g) + b.
+template <int DIMS, int CH, bool ROT>
 __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, const float4 &q01,
-                                       const float4 &q11, const CellPairs &a, const Staged &st,
-                                       int base, int RW, Acc &acc) {
+                                       const float4 &q11, const CellPairs &a, const RotPairs &rot,
+                                       const Staged &st, int base, int RW, Acc &acc) {
   float2 d = __fmul2_rn(a.a00, lo2(q00));
   float2 w = __fmul2_rn(a.a00, hi2(q00));
   d = __ffma2_rn(a.a10, lo2(q10), d);
@@ -110,6 +117,8 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
     d = __ffma2_rn(a.a11, lo2(q11), d);
     w = __ffma2_rn(a.a11, hi2(q11), w);
   }
+  // (dx, dy) -> (dx cos - dy sin, dx sin + dy cos)
+  if (ROT) d = __ffma2_rn(make_float2(d.x, d.x), rot.c, __fmul2_rn(make_float2(d.y, d.y), rot.s));
   // integer part n = round-to-nearest(d - 1/2) (= floor(d) except at exact
   // integers, where bilinear sampling gives the same value either way) and
   // fraction f = d - n in [0, 1], for both axes at once; see split_offset.
@@ -121,7 +130,11 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   // NaN to the first node), and every node tap satisfies |o| <= R, the layer
   // reach; so the blended |d| <= R (1 + 2^-21) and n = round(d - 1/2) lies in
   // [-ceil(R) - 1, ceil(R)] = [-halo, halo - 1], which with the corner n + 1
-  // keeps every read inside the staged tile + halo region.
+  // keeps every read inside the staged tile + halo region.  The rotated
+  // variant takes R as the largest Euclidean tap length (the norm of a convex
+  // blend is at most the largest node norm) and normalises (cos, sin) to unit
+  // length, so each rotated component is within R (1 + 2^-20): the same
+  // argument holds.
   const int nx = __float_as_int(r.x) - 0x4B400000;
   const int ny = __float_as_int(r.y) - 0x4B400000;
   const int e = base + ny * RW + nx;
@@ -135,7 +148,7 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   add_corner<CH>(st, e + RW + 1, w11, acc);
 }
 
-template <int DIMS, int SRC, int DST, int NP, int CH, int PIX>
+template <int DIMS, int SRC, int DST, int NP, int CH, int PIX, bool ROT>
 __global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : 3)
 sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   constexpr int kSvPix = PIX, kSvTileH = PIX * kSvWarps;
@@ -168,6 +181,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   const int T = P.T;
   Cell c[kSvPix];
   CellPairs cp[kSvPix];
+  RotPairs rp[kSvPix];
   int base[kSvPix];
   Acc acc[kSvPix];
   bool same = true;
@@ -177,6 +191,18 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     const int yc = min(ty0 + r, P.H - 1);
     c[j] = make_cell<DIMS>(P.ax, P.maps, HW, (long long)yc * P.W + xc);
     cp[j] = cell_pairs(c[j]);
+    if (ROT) {
+      float phi = __ldg(P.angle + (long long)yc * P.W + xc);
+      if (!isfinite(phi)) phi = 0.f;
+      float sn, cs;
+      sincosf(phi, &sn, &cs);
+      const float inv = rsqrtf(fmaf(cs, cs, sn * sn));
+      cs *= inv;
+      sn *= inv;
+      rp[j] = {make_float2(cs, sn), make_float2(-sn, cs)};
+    } else {
+      rp[j] = {make_float2(1.f, 0.f), make_float2(0.f, 1.f)};
+    }
     base[j] = (r + halo) * RW + (lane + halo);
     acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
     same = same && (c[j].n00 == c[0].n00);
@@ -190,7 +216,8 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
       const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
       const float4 q11 = DIMS == 2 ? node_tap(P, b11 + i) : q10;
 #pragma unroll
-      for (int j = 0; j < kSvPix; ++j) sv_tap<DIMS, CH>(q00, q10, q01, q11, cp[j], st, base[j], RW, acc[j]);
+      for (int j = 0; j < kSvPix; ++j)
+        sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
     }
   } else {
     // unrolled so the per-pixel arrays stay in registers
@@ -202,7 +229,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
         const float4 q00 = node_tap(P, b00 + i), q10 = node_tap(P, b10 + i);
         const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
         const float4 q11 = DIMS == 2 ? node_tap(P, b11 + i) : q10;
-        sv_tap<DIMS, CH>(q00, q10, q01, q11, cp[j], st, base[j], RW, acc[j]);
+        sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
       }
     }
   }
@@ -217,9 +244,9 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   }
 }
 
-template <int DIMS, int SRC, int DST, int NP, int CH, int PIX>
+template <int DIMS, int SRC, int DST, int NP, int CH, int PIX, bool ROT>
 int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
-  auto k = sv_layer_kernel<DIMS, SRC, DST, NP, CH, PIX>;
+  auto k = sv_layer_kernel<DIMS, SRC, DST, NP, CH, PIX, ROT>;
   constexpr int kSvTileH = PIX * kSvWarps;
   const size_t smem = (size_t)P.region_w * (kSvTileH + 2 * P.halo) * sv_stage_bytes(CH);
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
@@ -237,33 +264,34 @@ int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
 }
 
 // Storage combination of one layer: (source kind, destination kind), tile
-// configuration pix (2 or 4 pixels per thread).
-template <int DIMS, int NP>
+// configuration pix (2 or 4 pixels per thread); ROT selects the rotated
+// variant (P.angle set).
+template <int DIMS, int NP, bool ROT>
 int launch_sv_layer(int src, int dst, int C, const SvLayerParams<NP> &P, cudaStream_t s, int pix);
 
-#define DISK_SV_CASE(DIMS, NP, S, D)                                                        \
+#define DISK_SV_CASE(DIMS, NP, ROT, S, D)                                                   \
   if (src == S && dst == D) {                                                               \
     if (pix == 4)                                                                           \
-      return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4, 4>(P, s)                             \
-                : launch_sv_layer_t<DIMS, S, D, NP, 3, 4>(P, s);                            \
-    return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4, 2>(P, s)                               \
-              : launch_sv_layer_t<DIMS, S, D, NP, 3, 2>(P, s);                              \
+      return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4, 4, ROT>(P, s)                        \
+                : launch_sv_layer_t<DIMS, S, D, NP, 3, 4, ROT>(P, s);                       \
+    return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4, 2, ROT>(P, s)                          \
+              : launch_sv_layer_t<DIMS, S, D, NP, 3, 2, ROT>(P, s);                         \
   }
 
 // FP32 images: FP32 planes; FP16 images: FP16 planes (see intermediate_kind).
-#define DISK_SV_INSTANTIATE(DIMS, NP)                                                       \
+#define DISK_SV_INSTANTIATE(DIMS, NP, ROT)                                                  \
   template <>                                                                               \
-  int launch_sv_layer<DIMS, NP>(int src, int dst, int C, const SvLayerParams<NP> &P,          \
-                                cudaStream_t s, int pix) {                                  \
+  int launch_sv_layer<DIMS, NP, ROT>(int src, int dst, int C, const SvLayerParams<NP> &P,     \
+                                     cudaStream_t s, int pix) {                             \
     const bool c4 = C == 4;                                                                 \
-    DISK_SV_CASE(DIMS, NP, PIX_F32, PIX_RGBA32)                                             \
-    DISK_SV_CASE(DIMS, NP, PIX_RGBA32, PIX_RGBA32)                                          \
-    DISK_SV_CASE(DIMS, NP, PIX_RGBA32, PIX_F32)                                             \
-    DISK_SV_CASE(DIMS, NP, PIX_F32, PIX_F32)                                                \
-    DISK_SV_CASE(DIMS, NP, PIX_F16, PIX_RGBA16)                                             \
-    DISK_SV_CASE(DIMS, NP, PIX_RGBA16, PIX_RGBA16)                                          \
-    DISK_SV_CASE(DIMS, NP, PIX_RGBA16, PIX_F16)                                             \
-    DISK_SV_CASE(DIMS, NP, PIX_F16, PIX_F16)                                                \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_F32, PIX_RGBA32)                                        \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA32, PIX_RGBA32)                                     \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA32, PIX_F32)                                        \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_F32, PIX_F32)                                           \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_F16, PIX_RGBA16)                                        \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA16, PIX_RGBA16)                                     \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA16, PIX_F16)                                        \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_F16, PIX_F16)                                           \
     return fail(DISK_ERR_INVALID_ARG, "unsupported layer storage combination");            \
   }
 

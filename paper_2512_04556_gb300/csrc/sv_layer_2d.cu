@@ -2,6 +2,6 @@
 #include "sv_layer.cuh"
 
 namespace disk {
-DISK_SV_INSTANTIATE(2, kSvParamTaps)
-DISK_SV_INSTANTIATE(2, 0)
+DISK_SV_INSTANTIATE(2, kSvParamTaps, false)
+DISK_SV_INSTANTIATE(2, 0, false)
 }  // namespace disk

@@ -1,0 +1,7 @@
+// Instantiations of the rotated spatially varying layer kernel for 2-D bases.
+#include "sv_layer.cuh"
+
+namespace disk {
+DISK_SV_INSTANTIATE(2, kSvParamTaps, true)
+DISK_SV_INSTANTIATE(2, 0, true)
+}  // namespace disk

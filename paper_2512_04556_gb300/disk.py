@@ -65,6 +65,9 @@ def lib() -> ctypes.CDLL:
                                              _vp, _vp]),
             "disk_sv_filter_autotune": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _ip, _vp]),
             "disk_sv_filter_set_tile": (_i, [_vp, _i, _i, _i, _i, _i]),
+            "disk_sv_filter_rotated": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp, _vp]),
+            "disk_sv_filter_rotated_autotune": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp,
+                                                     _vp, _ip, _vp]),
             "disk_sv_filter_noalloc": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp]),
             "disk_dense_sv": (_i, [_i, _ip, _fp, _vp, _i, _vp, _sz, _vp, _sz, _i, _i, _i, _i,
                                    _vp, _vp]),
@@ -221,6 +224,42 @@ def sv_filter_autotune(basis: Basis, img, maps, out=None, stream=None) -> list:
     _check("disk_sv_filter_autotune", lib().disk_sv_filter_autotune(
         basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
         _vp(maps.data_ptr()), chosen, _stream(stream)))
+    return list(chosen)
+
+
+def _angle_arg(angle, H: int, W: int):
+    import torch
+    if (angle.dtype != torch.float32 or not angle.is_cuda or not angle.is_contiguous()
+            or angle.numel() != H * W):
+        raise ValueError("angle must be a contiguous float32 CUDA tensor of H x W values")
+    return _vp(angle.data_ptr())
+
+
+def sv_filter_rotated(basis: Basis, img, maps, angle, out=None, stream=None):
+    """sv_filter with every pixel's blended tap offsets turned by angle [H, W]
+    (float32 radians, x right, y down)."""
+    import torch
+    ip, ipitch, H, W, C = _image_args(img)
+    if out is None:
+        out = torch.empty_like(img, memory_format=torch.contiguous_format)
+    op, opitch, *_ = _image_args(out)
+    _check("disk_sv_filter_rotated", lib().disk_sv_filter_rotated(
+        basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
+        _vp(maps.data_ptr()), _angle_arg(angle, H, W), _stream(stream)))
+    return out
+
+
+def sv_filter_rotated_autotune(basis: Basis, img, maps, angle, out=None, stream=None) -> list:
+    """Tile autotuner of sv_filter_rotated; returns pixels per thread per layer."""
+    import torch
+    ip, ipitch, H, W, C = _image_args(img)
+    if out is None:
+        out = torch.empty_like(img, memory_format=torch.contiguous_format)
+    op, opitch, *_ = _image_args(out)
+    chosen = (ctypes.c_int * basis.L)()
+    _check("disk_sv_filter_rotated_autotune", lib().disk_sv_filter_rotated_autotune(
+        basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
+        _vp(maps.data_ptr()), _angle_arg(angle, H, W), chosen, _stream(stream)))
     return list(chosen)
 
 

@@ -198,6 +198,42 @@ def ellipse_params(radius: float, u: float) -> tuple[float, float, float]:
     return radius, 1.0 + 3.0 * u, math.pi * u
 
 
+def line(length: float, K: int | None = None, angle: float = 0.0, width: float = 1.0) -> np.ndarray:
+    """Motion-blur segment: |along| <= length / 2, |across| <= width / 2, the
+    long axis at ``angle`` (x right, y down); size 2 ceil(length / 2) + 1."""
+    K = K or kernel_size_for(length / 2.0)
+    xx, yy = _grid(K)
+    c, s = math.cos(angle), math.sin(angle)
+    along = c * xx + s * yy
+    across = -s * xx + c * yy
+    return _coverage((np.abs(along) <= length / 2.0) & (np.abs(across) <= width / 2.0), K)
+
+
+def cat_eye(radius: float, K: int | None = None, angle: float = 0.0) -> np.ndarray:
+    """Rotational-bokeh kernel: an ellipse of semi-major radius and
+    semi-minor radius / 2, major axis at ``angle``."""
+    return ellipse(radius, 2.0, angle, K)
+
+
+def radial_maps(H: int, W: int, lo: float, hi: float, tangential: bool = False,
+                seed: int = SEED_MAP) -> tuple[np.ndarray, np.ndarray]:
+    """Strength and angle maps of the radial effects: strength grows from lo
+    at the frame centre to hi at the corners (plus a faint smooth
+    perturbation); the angle (radians, x right, y down) points away from the
+    centre (radial motion blur) or across that direction (rotational bokeh).
+    Returns float32 [H][W] strength and float32 [H][W] angle."""
+    y = np.arange(H)[:, None] - (H - 1) / 2.0
+    x = np.arange(W)[None, :] - (W - 1) / 2.0
+    r = np.sqrt(x * x + y * y)
+    t = r / r.max()
+    pert = 0.05 * (smooth_field(H, W, 96.0, seed, stream=9) - 0.5)
+    strength = np.clip(lo + (hi - lo) * (t + pert), lo, hi).astype(np.float32)
+    ang = np.arctan2(np.broadcast_to(y, (H, W)), np.broadcast_to(x, (H, W)))
+    if tangential:
+        ang = ang + np.pi / 2
+    return strength, ang.astype(np.float32)
+
+
 def ring(radius: float, width: float, K: int | None = None) -> np.ndarray:
     K = K or kernel_size_for(radius)
     xx, yy = _grid(K)
@@ -290,6 +326,12 @@ C4 = dict(name="sv_4k_fp16_2d", H=2160, W=3840, C=3, L=4, T=24,
           map_range0=(2.0, 40.0), map_range1=(0.0, 1.0), map_sigma=192.0, dense_K=81)
 G = dict(name="sv_4k_fp16_gaussian_tilt_shift", H=2160, W=3840, C=3, L=6, T=8,
          nodes=list(np.linspace(1.0, 11.0, 11)), map_range=(1.0, 11.0), dense_K=67)
+RM = dict(name="sv_4k_fp16_radial_motion", H=2160, W=3840, C=3, L=3, T=8,
+          nodes=list(np.linspace(2.0, 40.0, 12)), map_range=(2.0, 40.0), dense_K=41,
+          dense_angles=37)
+RB = dict(name="sv_4k_fp16_rotational_bokeh", H=2160, W=3840, C=3, L=4, T=16,
+          nodes=list(np.linspace(2.0, 24.0, 12)), map_range=(2.0, 24.0), dense_K=49,
+          dense_angles=37)
 C5 = dict(name="mlp_init", train=50000, heldout=2000, L=4, T=16, hidden=512, depth=3, side=64)
 
 

@@ -12,10 +12,14 @@ radial initialisation.
   bases/disk16_L4T16.dkb    16 disks, radius 1..32 px, L=4, T=16 (1-D)
   bases/gauss11_L6T8.dkb    11 Gaussians, sigma 1..11 px, L=6, T=8 (1-D; the paper's
                             6-layer, 8-sample configuration)
+  bases/line12_L3T8.dkb     12 motion-blur segments, length 2..40 px, along x, L=3, T=8 (1-D;
+                            turned per pixel at run time for radial motion blur)
+  bases/cateye12_L4T16.dkb  12 ellipses of aspect 2, semi-major 2..24 px, along x, L=4, T=16
+                            (1-D; turned per pixel at run time for rotational bokeh)
   bases/ellipse8x8_L4T24.dkb  8 x 8 ellipses, radius 2..40 px x u in [0,1]
                             (anisotropy 1+3u, rotation pi u), L=4, T=24 (2-D)
 
-Usage: python tests/golden/make_bases.py [--steps N] [--only disk|ellipse|gauss]
+Usage: python tests/golden/make_bases.py [--steps N] [--only disk|ellipse|gauss|line|cateye]
 """
 import json
 import math
@@ -41,6 +45,10 @@ def _chain(args):
             tgt = wl.disk(r)
         elif kind == "gauss":
             tgt = wl.gaussian(r)
+        elif kind == "line":
+            tgt = wl.line(r)
+        elif kind == "cateye":
+            tgt = wl.cat_eye(r)
         else:
             tgt = wl.ellipse(*wl.ellipse_params(r, u))
         K = tgt.shape[0]
@@ -71,8 +79,10 @@ def main(steps=1000, only=None):
     jobs = [("disk", list(c2["nodes"]), 0.0, c2["L"], c2["T"], steps)]
     jobs += [("ellipse", list(c4["nodes0"]), float(u), c4["L"], c4["T"], steps) for u in c4["nodes1"]]
     jobs += [("gauss", list(g["nodes"]), 0.0, g["L"], g["T"], steps)]
+    jobs += [("line", list(wl.RM["nodes"]), 0.0, wl.RM["L"], wl.RM["T"], steps)]
+    jobs += [("cateye", list(wl.RB["nodes"]), 0.0, wl.RB["L"], wl.RB["T"], steps)]
     if only:
-        jobs = [j for j in jobs if j[0] == only]
+        jobs = [j for j in jobs if j[0] in only.split(",")]
     os.environ["OMP_NUM_THREADS"] = "1"
     t0 = time.time()
     with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 4)) as pool:
@@ -89,6 +99,12 @@ def main(steps=1000, only=None):
         gth = [r for r in res if r[0] == "gauss"][0]
         basis_io.write(os.path.join(OUT, "gauss11_L6T8.dkb"), [g["nodes"]], np.stack(gth[2]))
         report["gauss"] = gth[3]
+    for kind, preset, fname in (("line", wl.RM, "line12_L3T8.dkb"),
+                                ("cateye", wl.RB, "cateye12_L4T16.dkb")):
+        if kind in kinds:
+            th = [r for r in res if r[0] == kind][0]
+            basis_io.write(os.path.join(OUT, fname), [preset["nodes"]], np.stack(th[2]))
+            report[kind] = th[3]
     if "ellipse" in kinds:
         ell = {r[1]: r for r in res if r[0] == "ellipse"}
         th = np.zeros((8, 8, c4["L"], c4["T"], 3))

@@ -129,6 +129,46 @@ def test_4k_fp16_gaussian_tilt_shift_sampled(torch_cuda):
     assert np.abs(got - want).max() / np.abs(want).max() <= 2e-3
 
 
+def _cone_rot(theta):
+    return int(sum(np.ceil(np.hypot(theta[:, l, :, 0], theta[:, l, :, 1]).max()) + 1
+                   for l in range(theta.shape[1])))
+
+
+@pytest.mark.parametrize("preset,fname,tangential", [
+    (wl.RM, "line12_L3T8.dkb", False), (wl.RB, "cateye12_L4T16.dkb", True)])
+def test_4k_fp16_rotated_sampled(torch_cuda, preset, fname, tangential):
+    """3840 x 2160 FP16, radial motion blur (segments 2..40 px, L=3, T=8) and
+    rotational bokeh (aspect-2 ellipses 2..24 px, L=4, T=16): a 1-D basis
+    over strength turned per pixel by the radial / tangential angle map,
+    autotuned tiles as the benchmark's legs."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    H, W = preset["H"], preset["W"]
+    img = wl.to_fp16(wl.image_rects(H, W, 3))
+    strength, angle = wl.radial_maps(H, W, *preset["map_range"], tangential=tangential)
+    maps = strength[None]
+    path = os.path.join(BASES, fname)
+    b = disk.Basis.load(path)
+    di, dm, da = (torch.from_numpy(img).cuda(), torch.from_numpy(maps).cuda(),
+                  torch.from_numpy(angle).cuda())
+    disk.sv_filter_rotated_autotune(b, di, dm, da)
+    out = disk.sv_filter_rotated(b, di, dm, da).cpu().numpy()
+    axes, th = basis_io.read(path)
+    th = th.astype(np.float64)
+    R = _cone_rot(th)
+    nv = axes[0].astype(np.float64)
+    got, want = [], []
+    for (y, x) in _samples(H, W, 20, 4):
+        y0, y1, x0, x1 = max(0, y - R), min(H, y + R + 1), max(0, x - R), min(W, x + R + 1)
+        o = oracle.sv_filter_rotated(img[y0:y1, x0:x1].astype(np.float64),
+                                     maps[:, y0:y1, x0:x1].astype(np.float64),
+                                     angle[y0:y1, x0:x1].astype(np.float64), [len(nv)], nv, th)
+        want.append(np.float16(o[y - y0, x - x0]).astype(np.float64))
+        got.append(out[y, x].astype(np.float64))
+    got, want = np.array(got), np.array(want)
+    assert np.abs(got - want).max() / np.abs(want).max() <= 2e-3
+
+
 def test_1080p_fp32_1d_filter_sampled(torch_cuda):
     """1920 x 1080 FP32, 16 fitted disks (radius 1..32), L=4, T=16."""
     torch = torch_cuda
