@@ -357,6 +357,10 @@ def rotated_leg(preset, basis_file, tangential, d_img, flush, stream):
     d_out = torch.empty_like(d_img)
     ms = _timed(lambda: disk.sv_filter_rotated(b, d_img, d_s, d_a, out=d_out, stream=stream),
                 flush, stream, 10)
+    # the same basis and strength map without the turn: the rotation's cost
+    d_plain = torch.empty_like(d_img)
+    disk.sv_filter_autotune(b, d_img, d_s, out=d_plain, stream=stream)
+    pms = _timed(lambda: disk.sv_filter(b, d_img, d_s, out=d_plain, stream=stream), flush, stream, 10)
     s_nodes = np.linspace(*preset["map_range"], 16)
     a_nodes = np.linspace(0.0, np.pi, preset["dense_angles"])
     K = preset["dense_K"]
@@ -371,6 +375,7 @@ def rotated_leg(preset, basis_file, tangential, d_img, flush, stream):
     return {"value": px / (ms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": ms,
             "L": b.L, "T": b.T, "nodes": f"{b.n_nodes[0]} along the strength axis, turned per pixel",
             "tile": ", ".join(f"32x{8 * p}" for p in tiles),
+            "unrotated_ms": pms, "rotation_overhead": ms / pms - 1.0,
             "dense_ms": dms, "dense_kernel": f"{K}x{K}, 16 strengths x {len(a_nodes)} angles",
             "speedup_disk_vs_dense": dms / ms,
             "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20)))}

@@ -5,6 +5,8 @@
 #include <cstring>
 #include <memory>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace disk {
@@ -21,6 +23,37 @@ int cuda_fail(cudaError_t e, const char *what) {
   std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" +
                   cudaGetErrorString(e) + ")";
   return fail(e == cudaErrorMemoryAllocation ? DISK_ERR_OOM : DISK_ERR_CUDA, m);
+}
+
+cudaError_t scratch_alloc_raw(void **p, size_t bytes, cudaStream_t s) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t np;
+      e = cudaMemPoolCreate(&np, &props);
+      if (e != cudaSuccess) return e;
+      unsigned long long keep = ~0ull;
+      e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(np);
+        return e;
+      }
+      pools[dev] = np;
+    }
+    pool = pools[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 void make_axes(int dims, const int *n_nodes, const float *node_vals, AxisNodes ax[2]) {

@@ -147,8 +147,8 @@ extern "C" int disk_dense_sv(int dims, const int *n_nodes, const float *node_val
   P.region_w = kTileW + 2 * P.hd;
   make_axes(dims, n_nodes, node_vals, P.ax);
   int *d_hw = nullptr;
-  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&d_hw), sizeof(int) * B, s),
-                "cudaMallocAsync(dense extents)");
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&d_hw), sizeof(int) * B, s),
+                "scratch_alloc(dense extents)");
   node_extent_kernel<<<B, 256, 0, s>>>(d_lut, Kd, d_hw);
   rc = DISK_OK;
   cudaError_t e = cudaGetLastError();

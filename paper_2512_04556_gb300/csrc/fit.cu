@@ -495,7 +495,7 @@ int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, i
   const size_t head = ((meta_bytes + order_bytes + 255) / 256) * 256;
   const size_t bytes = head + plan.scratch_floats * sizeof(float) + plan.idx_ints * sizeof(int);
   char *buf = nullptr;
-  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, s), "cudaMallocAsync(fit scratch)");
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&buf), bytes, s), "scratch_alloc(fit scratch)");
   // The plan rides in kernel parameters (no host staging buffer, no sync), so
   // the whole call can be captured in a CUDA graph.
   cudaError_t e = cudaSuccess;
@@ -570,7 +570,7 @@ extern "C" int disk_fit_autotune(const float *d_targets, const int *sizes, int b
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float *theta = nullptr;
   const size_t tb = (size_t)batch * L * T * 3 * sizeof(float);
-  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&theta), tb, s), "cudaMallocAsync(autotune)");
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&theta), tb, s), "scratch_alloc(autotune)");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);

@@ -37,6 +37,17 @@ int fail(int code, const std::string &msg);
 // Maps a CUDA error to DISK_ERR_OOM / DISK_ERR_CUDA with a detail message.
 int cuda_fail(cudaError_t e, const char *what);
 
+// Stream-ordered scratch from the library's own memory pool on the current
+// device.  The pool keeps freed memory mapped (release threshold: no limit),
+// so a frame loop that synchronises between calls does not map and unmap its
+// scratch every frame, as the default pool would at each synchronisation.
+// Free with cudaFreeAsync.  Capturable into CUDA graphs.
+cudaError_t scratch_alloc_raw(void **p, size_t bytes, cudaStream_t s);
+template <class T>
+inline cudaError_t scratch_alloc(T **p, size_t bytes, cudaStream_t s) {
+  return scratch_alloc_raw(reinterpret_cast<void **>(p), bytes, s);
+}
+
 inline int halo_of(float reach) {
   // Offsets with |o| <= reach touch pixels within ceil(reach) + 1 of the
   // output pixel (the +1 is the bilinear footprint).

@@ -272,8 +272,8 @@ extern "C" int disk_mlp_forward(const float *d_params, int n_in, int hidden, int
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float *ping = nullptr;
   if (sh.depth > 0)
-    DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&ping), 2ull * batch * sh.hidden * sizeof(float), s),
-                  "cudaMallocAsync(mlp forward)");
+    DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&ping), 2ull * batch * sh.hidden * sizeof(float), s),
+                  "scratch_alloc(mlp forward)");
   rc = mlp_forward(sh, d_params, d_x, batch, d_y, nullptr, ping, s);
   if (ping) cudaFreeAsync(ping, s);
   return rc;
@@ -293,7 +293,7 @@ extern "C" int disk_mlp_train_step(float *d_params, float *d_m, float *d_v, int 
   const long long wmax = std::max(sh.hidden, n_out);
   const size_t bytes = sizeof(float) * (nacts + ny + 2 * batch * wmax + np);
   float *buf = nullptr;
-  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, s), "cudaMallocAsync(mlp train)");
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&buf), bytes, s), "scratch_alloc(mlp train)");
   float *acts = buf, *y = acts + nacts, *d0 = y + ny, *d1 = d0 + batch * wmax, *grad = d1 + batch * wmax;
   rc = mlp_forward(sh, d_params, d_x, batch, y, acts, nullptr, s);
   cudaError_t e = cudaSuccess;
@@ -346,7 +346,7 @@ extern "C" int disk_downsample_targets(const float *d_targets, const int *sizes,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char *buf = nullptr;
   const size_t bytes = batch * (sizeof(long long) + sizeof(int));
-  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, s), "cudaMallocAsync(downsample)");
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&buf), bytes, s), "scratch_alloc(downsample)");
   // small host tables: a pageable copy returns once the data is staged
   cudaError_t e = cudaMemcpyAsync(buf, offs.data(), batch * sizeof(long long), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)

@@ -391,7 +391,7 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
                           cudaStream_t s) {
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
-  P.angle = nullptr;
+  P.rot = nullptr;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16, mid = intermediate_kind(dtype);
@@ -445,10 +445,10 @@ extern "C" int disk_sv_filter_backward_image(const disk_basis *b, const void *d_
   float4 *bufs[2] = {nullptr, nullptr};
   const int nbuf = b->L >= 2 ? 2 : 1;
   for (int i = 0; i < nbuf; ++i) {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&bufs[i]), plane, s);
+    cudaError_t e = scratch_alloc(reinterpret_cast<void **>(&bufs[i]), plane, s);
     if (e != cudaSuccess) {
       if (i) cudaFreeAsync(bufs[0], s);
-      return cuda_fail(e, "cudaMallocAsync(backward planes)");
+      return cuda_fail(e, "scratch_alloc(backward planes)");
     }
   }
   static thread_local BwParams P;
@@ -512,7 +512,7 @@ extern "C" int disk_sv_filter_backward(const disk_basis *b, const void *d_in, si
   const size_t act_plane = (size_t)H * W * kind_bytes(mid), g_plane = (size_t)H * W * sizeof(float4);
   const size_t bytes = (size_t)(L - 1) * act_plane + 2 * g_plane;
   char *buf = nullptr;
-  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&buf), bytes, s), "cudaMallocAsync(backward)");
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&buf), bytes, s), "scratch_alloc(backward)");
   char *acts[DISK_MAX_LAYERS];
   for (int l = 0; l + 1 < L; ++l) acts[l] = buf + (size_t)l * act_plane;
   float4 *gpl[2] = {reinterpret_cast<float4 *>(buf + (size_t)(L - 1) * act_plane),

@@ -5,9 +5,25 @@
 // storage precision (FP32 or FP16) taken from the stream-ordered pool; the
 // first layer reads the caller's image and the last writes the caller's
 // output.
+#include <algorithm>
+
 #include "sv_layer.cuh"
 
 namespace disk {
+
+__global__ void rotation_kernel(const float *__restrict__ angle, float2 *__restrict__ rot,
+                                long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float phi = angle[i];
+    if (!isfinite(phi)) phi = 0.f;
+    float sn, cs;
+    sincosf(phi, &sn, &cs);
+    const float inv = rsqrtf(fmaf(cs, cs, sn * sn));
+    rot[i] = make_float2(cs * inv, sn * inv);
+  }
+}
+
 namespace {
 
 template <int NP>
@@ -17,7 +33,7 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   // The parameter block is large; keep it off the host stack.
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
-  P.angle = d_angle;
+  P.rot = nullptr;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
@@ -28,13 +44,29 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   const size_t plane = (size_t)H * W * mid_bytes;
   const int nbuf = L >= 3 ? 2 : (L == 2 ? 1 : 0);
   for (int i = 0; i < nbuf; ++i) {
-    cudaError_t e = cudaMallocAsync(&bufs[i], plane, s);
+    cudaError_t e = scratch_alloc(&bufs[i], plane, s);
     if (e != cudaSuccess) {
       if (i) cudaFreeAsync(bufs[0], s);
-      return cuda_fail(e, "cudaMallocAsync(sv_filter scratch)");
+      return cuda_fail(e, "scratch_alloc(sv_filter scratch)");
     }
   }
+  float2 *rot = nullptr;
+  if (d_angle) {
+    const long long n = (long long)H * W;
+    cudaError_t e = scratch_alloc(&rot, (size_t)n * sizeof(float2), s);
+    if (e != cudaSuccess) {
+      for (int i = 0; i < nbuf; ++i) cudaFreeAsync(bufs[i], s);
+      return cuda_fail(e, "scratch_alloc(rotation plane)");
+    }
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+    rotation_kernel<<<blocks, 256, 0, s>>>(d_angle, rot, n);
+    P.rot = rot;
+  }
   int rc = DISK_OK;
+  if (d_angle) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) rc = cuda_fail(e, "launch rotation_kernel");
+  }
   for (int l = 0; l < L && rc == DISK_OK; ++l) {
     P.halo = halo_of(layer_reach(b, l, d_angle != nullptr));
     P.region_w = kSvTileW + 2 * P.halo;
@@ -64,6 +96,7 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   }
   if (ev && rc == DISK_OK) cudaEventRecord(ev[L], s);
   for (int i = 0; i < nbuf; ++i) cudaFreeAsync(bufs[i], s);
+  if (rot) cudaFreeAsync(rot, s);
   return rc;
 }
 

@@ -43,7 +43,7 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
                 float4 *planes, cudaStream_t s) {
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
-  P.angle = nullptr;
+  P.rot = nullptr;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;

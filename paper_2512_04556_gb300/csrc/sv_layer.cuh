@@ -40,7 +40,7 @@ struct SvLayerParams {
   void *dst;
   long long dst_pitch;
   const float *maps;
-  const float *angle;   // [H][W] radians, rotated variant only
+  const float2 *rot;    // [H][W] (cos, sin) of each pixel's angle, rotated variant only
   const float4 *gtaps;  // [B][T] of this layer when NP == 0: (dx, dy, w, w)
   int H, W, C, T, halo, region_w;
   AxisNodes ax[2];
@@ -132,9 +132,9 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   // [-ceil(R) - 1, ceil(R)] = [-halo, halo - 1], which with the corner n + 1
   // keeps every read inside the staged tile + halo region.  The rotated
   // variant takes R as the largest Euclidean tap length (the norm of a convex
-  // blend is at most the largest node norm) and normalises (cos, sin) to unit
-  // length, so each rotated component is within R (1 + 2^-20): the same
-  // argument holds.
+  // blend is at most the largest node norm) and reads (cos, sin) normalised
+  // to unit length by rotation_kernel, so each rotated component is within
+  // R (1 + 2^-20): the same argument holds.
   const int nx = __float_as_int(r.x) - 0x4B400000;
   const int ny = __float_as_int(r.y) - 0x4B400000;
   const int e = base + ny * RW + nx;
@@ -192,14 +192,8 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     c[j] = make_cell<DIMS>(P.ax, P.maps, HW, (long long)yc * P.W + xc);
     cp[j] = cell_pairs(c[j]);
     if (ROT) {
-      float phi = __ldg(P.angle + (long long)yc * P.W + xc);
-      if (!isfinite(phi)) phi = 0.f;
-      float sn, cs;
-      sincosf(phi, &sn, &cs);
-      const float inv = rsqrtf(fmaf(cs, cs, sn * sn));
-      cs *= inv;
-      sn *= inv;
-      rp[j] = {make_float2(cs, sn), make_float2(-sn, cs)};
+      const float2 r = __ldg(P.rot + (long long)yc * P.W + xc);
+      rp[j] = {r, make_float2(-r.y, r.x)};
     } else {
       rp[j] = {make_float2(1.f, 0.f), make_float2(0.f, 1.f)};
     }
@@ -243,6 +237,11 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     }
   }
 }
+
+// (cos, sin) of every pixel's angle, once per filter call for all layers; a
+// non-finite angle acts as 0; the pair is scaled to unit length.
+__global__ void rotation_kernel(const float *__restrict__ angle, float2 *__restrict__ rot,
+                                long long n);
 
 template <int DIMS, int SRC, int DST, int NP, int CH, int PIX, bool ROT>
 int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {

@@ -101,8 +101,8 @@ extern "C" int disk_synth_kernel(const float *d_theta, int batch, int L, int T, 
   const size_t bytes = (size_t)batch * 2 * N * N * sizeof(float);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float *scratch = nullptr;
-  DISK_TRY_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&scratch), bytes, s),
-                "cudaMallocAsync(synth canvases)");
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&scratch), bytes, s),
+                "scratch_alloc(synth canvases)");
   const size_t smem = (size_t)L * T * sizeof(float4);
   synth_kernel<<<batch, kSynthThreads, smem, s>>>(d_theta, L, T, K, max_reach, R, scratch, d_out);
   cudaError_t e = cudaGetLastError();
