@@ -32,10 +32,16 @@ BASES = os.path.join(ROOT, "tests", "golden", "bases")
 C4_BASIS = os.path.join(BASES, "ellipse8x8_L4T24.dkb")
 BYTES_PER_PX = 20.0   # fused-pass algorithmic bytes: in 6 + out 6 + 2 maps x 4
 NOMINAL_HBM_GBS = 8000.0
+# Algorithmic FP32 operations (a multiply-add counts one) per pixel and tap of
+# a 2-D basis with 3 channels: the Eq. 9 blend of (dx, dy, w) over 4 nodes
+# (12), the integer/fraction split of the offset (4), the four bilinear
+# corner weights times w (8) and the 4 corners x 3 channels of Eq. 2 (12).
+OPS_PER_PX_TAP = 36
+# FP32 lanes: 152 SMs x 128 lanes, one operation per lane per clock.
+SMS, FP32_LANES_PER_SM = 152, 128
 # DRAM bytes (read + write) of one pass (the L = 4 sv_layer launches) of the
-# current kernel, from the ncu capture summarised in
-# profiles/sv_layer_4k_fp16_2d.md; set to None whenever the kernel changes.
-TRAFFIC_PER_PASS = 667.8e6
+# current kernel, from an ncu capture of it; None whenever the kernel changes.
+TRAFFIC_PER_PASS = None
 
 
 def parse():
@@ -192,16 +198,25 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     hbm = peaks.get("hbm_gbs")
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     out = {}
-    achieved = BYTES_PER_PX * px / (ms * 1e-3) / 1e9
-    out["roofline"] = {
-        "bound": "hbm", "achieved": achieved, "peak": hbm or 6800.0, "unit": "GB/s",
-        "frac": achieved / (hbm or 6800.0), "peak_source": "measured" if hbm else "fallback",
-        "frac_of_nominal_8tb": achieved / NOMINAL_HBM_GBS, "traffic": TRAFFIC_PER_PASS,
-        "kernel": "sv_layer_kernel (all L launches of one pass)",
-        "bytes_per_px": BYTES_PER_PX}
-    # shared-memory bound model: every tap reads four 16-byte corners
+    # The gather is bound by FP32 arithmetic and instruction issue, not by
+    # HBM: the roofline is the FP32 lane throughput at the maximum SM clock.
     taps = basis.L * basis.T
+    peak_tops = SMS * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved_tops = px * taps * OPS_PER_PX_TAP / (ms * 1e-3) / 1e12
+    achieved_gbs = BYTES_PER_PX * px / (ms * 1e-3) / 1e9
+    out["roofline"] = {
+        "bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s",
+        "frac": achieved_tops / peak_tops,
+        "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz",
+        "ops_per_px_tap": OPS_PER_PX_TAP, "taps_per_px": taps, "traffic": TRAFFIC_PER_PASS,
+        "kernel": "sv_layer_kernel (all L launches of one pass)",
+        "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm or 6800.0,
+                "frac": achieved_gbs / (hbm or 6800.0),
+                "peak_source": "measured" if hbm else "fallback",
+                "bytes_per_px": BYTES_PER_PX}}
+    # shared-memory bound model: every tap reads four 16-byte corners
     smem_bytes = px * taps * 4 * 16
     out["smem_model"] = {"bytes_per_pass": smem_bytes, "achieved_gbs": smem_bytes / (ms * 1e-3) / 1e9}
 

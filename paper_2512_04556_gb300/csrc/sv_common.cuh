@@ -104,18 +104,17 @@ struct Cell {
 };
 
 template <int DIMS>
-__device__ __forceinline__ Cell make_cell(const AxisNodes *ax, const float *maps, long long HW,
-                                          long long px) {
+__device__ __forceinline__ Cell make_cell_v(const AxisNodes *ax, float p0, float p1) {
   Cell c;
   int k0; float t0;
-  locate(ax[0], maps[px], k0, t0);
+  locate(ax[0], p0, k0, t0);
   const int k0b = min(k0 + 1, ax[0].n - 1);
   if (DIMS == 1) {
     c.n00 = k0; c.n10 = k0b; c.n01 = k0; c.n11 = k0b;
     c.a00 = 1.f - t0; c.a10 = t0; c.a01 = 0.f; c.a11 = 0.f;
   } else {
     int k1; float t1;
-    locate(ax[1], maps[HW + px], k1, t1);
+    locate(ax[1], p1, k1, t1);
     const int k1b = min(k1 + 1, ax[1].n - 1), n1 = ax[1].n;
     c.n00 = k0 * n1 + k1;  c.n01 = k0 * n1 + k1b;
     c.n10 = k0b * n1 + k1; c.n11 = k0b * n1 + k1b;
@@ -123,6 +122,12 @@ __device__ __forceinline__ Cell make_cell(const AxisNodes *ax, const float *maps
     c.a10 = t0 * (1.f - t1);         c.a11 = t0 * t1;
   }
   return c;
+}
+
+template <int DIMS>
+__device__ __forceinline__ Cell make_cell(const AxisNodes *ax, const float *maps, long long HW,
+                                          long long px) {
+  return make_cell_v<DIMS>(ax, maps[px], DIMS == 2 ? maps[HW + px] : 0.f);
 }
 
 // Splits an offset d into an integer n and a fraction f = d - n in [0, 1]

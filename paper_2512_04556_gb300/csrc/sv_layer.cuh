@@ -8,10 +8,11 @@
 // 32 lanes (consecutive columns) read consecutive entries.  FP16 images keep
 // FP16 planes in HBM; arithmetic and accumulation are FP32.
 // Every thread owns PIX pixels of one column (rows r, r+8, ...).
-// When all pixels of a warp sit in the same kernel-space cell -- the common
-// case, parameter maps being smooth -- the node taps of each tap index are
-// fetched once (warp-uniform constant-bank loads) and blended for the four
-// pixels with each pixel's own weights; other warps take the per-pixel path.
+// When each thread's pixels sit in one kernel-space cell -- the common case,
+// parameter maps being smooth -- the node taps of each tap index are fetched
+// once per thread (constant-bank loads) and blended for its pixels with each
+// pixel's own weights; warps with a thread whose pixels straddle cells take
+// the per-pixel path.
 #pragma once
 
 #include <type_traits>
@@ -160,25 +161,51 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   const int tx0 = blockIdx.x * kSvTileW, ty0 = blockIdx.y * kSvTileH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+  const int x = tx0 + lane, xc = min(x, P.W - 1);
+  const long long HW = (long long)P.H * P.W;
+  const int T = P.T;
+  // This thread's map values (and rotations), loaded before the staging so
+  // their latency overlaps its loads; the cells are formed after it.
+  float pv0[kSvPix], pv1[kSvPix];
+  float2 rv[kSvPix];
+#pragma unroll
+  for (int j = 0; j < kSvPix; ++j) {
+    const int yc = min(ty0 + warp + kSvWarps * j, P.H - 1);
+    const long long px = (long long)yc * P.W + xc;
+    pv0[j] = __ldg(P.maps + px);
+    pv1[j] = DIMS == 2 ? __ldg(P.maps + HW + px) : 0.f;
+    rv[j] = ROT ? __ldg(P.rot + px) : make_float2(1.f, 0.f);
+  }
   // Stage the source region, clamping coordinates to the image (Eq. 3 read
-  // with clamp-to-edge).
-  for (int ry = warp; ry < RH; ry += kSvWarps) {
-    const int gy = min(max(ty0 - halo + ry, 0), P.H - 1);
-    for (int rx = lane; rx < RW; rx += 32) {
-      const int gx = min(max(tx0 - halo + rx, 0), P.W - 1);
-      const float4 v = load_px<SRC>(P.src, P.src_pitch, P.C, gy, gx);
-      const int e = ry * RW + rx;
-      s_rg[e] = make_float2(v.x, v.y);
-      if (CH == 4) s_ba[e] = make_float2(v.z, v.w);
-      else s_b[e] = v.z;
+  // with clamp-to-edge).  Each warp takes rows warp, warp + 8, ...; four of
+  // its rows are loaded before any is converted and stored, so four global
+  // loads per thread are in flight instead of one.
+  constexpr int kStageRows = 4;
+  for (int rx = lane; rx < RW; rx += 32) {
+    const int gx = min(max(tx0 - halo + rx, 0), P.W - 1);
+    for (int ry0 = warp; ry0 < RH; ry0 += kSvWarps * kStageRows) {
+      float4 v[kStageRows];
+#pragma unroll
+      for (int u = 0; u < kStageRows; ++u) {
+        const int ry = ry0 + u * kSvWarps;
+        const int gy = min(max(ty0 - halo + ry, 0), P.H - 1);
+        if (ry < RH) v[u] = load_px<SRC>(P.src, P.src_pitch, P.C, gy, gx);
+      }
+#pragma unroll
+      for (int u = 0; u < kStageRows; ++u) {
+        const int ry = ry0 + u * kSvWarps;
+        if (ry < RH) {
+          const int e = ry * RW + rx;
+          s_rg[e] = make_float2(v[u].x, v[u].y);
+          if (CH == 4) s_ba[e] = make_float2(v[u].z, v[u].w);
+          else s_b[e] = v[u].z;
+        }
+      }
     }
   }
   __syncthreads();
   const Staged st{s_rg, s_b, s_ba};
 
-  const int x = tx0 + lane, xc = min(x, P.W - 1);
-  const long long HW = (long long)P.H * P.W;
-  const int T = P.T;
   Cell c[kSvPix];
   CellPairs cp[kSvPix];
   RotPairs rp[kSvPix];
@@ -187,24 +214,17 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   bool same = true;
 #pragma unroll
   for (int j = 0; j < kSvPix; ++j) {
-    const int r = warp + kSvWarps * j;
-    const int yc = min(ty0 + r, P.H - 1);
-    c[j] = make_cell<DIMS>(P.ax, P.maps, HW, (long long)yc * P.W + xc);
+    c[j] = make_cell_v<DIMS>(P.ax, pv0[j], pv1[j]);
     cp[j] = cell_pairs(c[j]);
-    if (ROT) {
-      const float2 r = __ldg(P.rot + (long long)yc * P.W + xc);
-      rp[j] = {r, make_float2(-r.y, r.x)};
-    } else {
-      rp[j] = {make_float2(1.f, 0.f), make_float2(0.f, 1.f)};
-    }
-    base[j] = (r + halo) * RW + (lane + halo);
+    rp[j] = {rv[j], make_float2(-rv[j].y, rv[j].x)};
+    base[j] = (warp + kSvWarps * j + halo) * RW + (lane + halo);
     acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
     same = same && (c[j].n00 == c[0].n00);
   }
   if (__all_sync(0xffffffffu, same)) {
-    // one node fetch per tap serves the thread's four pixels
+    // each thread's pixels share a cell: one node fetch per tap serves them
     const int b00 = c[0].n00 * T, b10 = c[0].n10 * T, b01 = c[0].n01 * T, b11 = c[0].n11 * T;
-#pragma unroll 1
+#pragma unroll 2
     for (int i = 0; i < T; ++i) {
       const float4 q00 = node_tap(P, b00 + i), q10 = node_tap(P, b10 + i);
       const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
