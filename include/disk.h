@@ -227,6 +227,24 @@ int disk_sv_filter_rotated_autotune(const disk_basis *basis, const void *d_in,
                                     int W, int C, int dtype, const float *d_maps,
                                     const float *d_angle, int *chosen, void *stream);
 
+/* Filters n_frames frames that live in host memory (the deployment form of
+ * disk_sv_filter: a video or burst whose frames arrive on the host).  Frame
+ * i: image h_in[i] (H x W x C, rows packed, dtype as disk_sv_filter), maps
+ * h_maps[i] (dims x H x W float32) -> h_out[i] (same layout as h_in[i]).
+ * The host-to-device copies of one frame and the device-to-host copy of
+ * another overlap the filtering of a third: two device slots alternate,
+ * copies run on two streams the call creates, the filter on `stream`, all
+ * ordered by events.  Host buffers should be page-locked (cudaHostAlloc or
+ * cudaHostRegister) for the copies to be asynchronous; every buffer must
+ * stay valid, and h_out untouched, until `stream` has completed (the call
+ * returns once the work is queued).  Output equals disk_sv_filter on the
+ * same frame with the same tile record.  Not capturable into a CUDA graph
+ * (it creates streams).  Ownership: all buffers caller-owned; the slots come
+ * from the library's pool. */
+int disk_sv_filter_frames(const disk_basis *basis, const void *const *h_in,
+                          void *const *h_out, const float *const *h_maps, int n_frames,
+                          int H, int W, int C, int dtype, void *stream);
+
 /* Records one tile configuration (pixels per thread: 2 or 4) for every
  * layer, for this (H, W, C, dtype), in the basis handle. */
 int disk_sv_filter_set_tile(const disk_basis *basis, int H, int W, int C, int dtype,

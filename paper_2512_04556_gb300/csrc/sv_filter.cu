@@ -242,6 +242,82 @@ extern "C" int disk_sv_filter_rotated_autotune(const disk_basis *b, const void *
                   static_cast<cudaStream_t>(stream));
 }
 
+extern "C" int disk_sv_filter_frames(const disk_basis *b, const void *const *h_in,
+                                     void *const *h_out, const float *const *h_maps,
+                                     int n_frames, int H, int W, int C, int dtype,
+                                     void *stream) {
+  if (!b) return fail(DISK_ERR_INVALID_ARG, "null basis");
+  if (n_frames < 0) return fail(DISK_ERR_INVALID_ARG, "negative frame count");
+  if (n_frames == 0) return DISK_OK;
+  if (!h_in || !h_out || !h_maps) return fail(DISK_ERR_INVALID_ARG, "null frame array");
+  for (int i = 0; i < n_frames; ++i)
+    if (!h_in[i] || !h_out[i] || !h_maps[i])
+      return fail(DISK_ERR_INVALID_ARG, "null host frame, output or map pointer");
+  if (H < 1 || W < 1 || H > 32768 || W > 32768 || (C != 3 && C != 4) ||
+      (dtype != DISK_F32 && dtype != DISK_F16))
+    return fail(DISK_ERR_INVALID_ARG, "bad frame shape or dtype");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t row = (size_t)W * C * (dtype == DISK_F32 ? 4 : 2);
+  const size_t img = row * H, map = (size_t)b->dims * H * W * sizeof(float);
+  // Two slots (input, output, maps) alternate between frames.
+  const int S = n_frames < 2 ? 1 : 2;
+  const size_t a256 = 256, slot = ((img + a256 - 1) / a256 * a256) * 2 + (map + a256 - 1) / a256 * a256;
+  char *buf = nullptr;
+  DISK_TRY_CUDA(scratch_alloc(&buf, slot * S, s), "scratch_alloc(frame slots)");
+  const void *d_in[2];
+  void *d_out[2];
+  const float *d_maps[2];
+  for (int k = 0; k < S; ++k) {
+    char *base = buf + slot * k;
+    d_in[k] = base;
+    d_out[k] = base + (img + a256 - 1) / a256 * a256;
+    d_maps[k] = reinterpret_cast<const float *>(base + 2 * ((img + a256 - 1) / a256 * a256));
+  }
+  int rc = check_filter_args(b, d_in[0], row, d_out[0], row, H, W, C, dtype, d_maps[0]);
+  cudaStream_t cin = nullptr, cout = nullptr;
+  cudaEvent_t ev[7] = {};  // alloc, in_ready[2], comp_done[2], out_done[2]
+  if (rc == DISK_OK) {
+    cudaError_t e = cudaStreamCreateWithFlags(&cin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cout, cudaStreamNonBlocking);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) rc = cuda_fail(e, "frame streams and events");
+  }
+  if (rc == DISK_OK) {
+    cudaEvent_t *in_ready = ev + 1, *comp_done = ev + 3, *out_done = ev + 5;
+    const std::vector<int> pix = layer_pix(b, H, W, C, dtype, false);
+    cudaEventRecord(ev[0], s);  // the slots exist on s from here on
+    cudaStreamWaitEvent(cin, ev[0], 0);
+    cudaStreamWaitEvent(cout, ev[0], 0);
+    for (int i = 0; i < n_frames && rc == DISK_OK; ++i) {
+      const int k = i % S;
+      if (i >= S) cudaStreamWaitEvent(cin, comp_done[k], 0);  // slot input consumed
+      cudaMemcpyAsync(const_cast<void *>(d_in[k]), h_in[i], img, cudaMemcpyHostToDevice, cin);
+      cudaMemcpyAsync(const_cast<float *>(d_maps[k]), h_maps[i], map, cudaMemcpyHostToDevice, cin);
+      cudaEventRecord(in_ready[k], cin);
+      cudaStreamWaitEvent(s, in_ready[k], 0);
+      if (i >= S) cudaStreamWaitEvent(s, out_done[k], 0);  // slot output read back
+      rc = filter_with(b, d_in[k], row, d_out[k], row, H, W, C, dtype, d_maps[k], nullptr, s,
+                       pix.data());
+      cudaEventRecord(comp_done[k], s);
+      cudaStreamWaitEvent(cout, comp_done[k], 0);
+      cudaMemcpyAsync(h_out[i], d_out[k], img, cudaMemcpyDeviceToHost, cout);
+      cudaEventRecord(out_done[k], cout);
+    }
+    for (int k = 0; k < S; ++k) cudaStreamWaitEvent(s, out_done[k], 0);
+    const cudaError_t e = cudaGetLastError();
+    if (rc == DISK_OK && e != cudaSuccess) rc = cuda_fail(e, "frame pipeline");
+  }
+  // Freed in stream order after the last read-back; streams and events are
+  // released by the runtime once their work has completed.
+  cudaFreeAsync(buf, s);
+  for (auto &x : ev)
+    if (x) cudaEventDestroy(x);
+  if (cin) cudaStreamDestroy(cin);
+  if (cout) cudaStreamDestroy(cout);
+  return rc;
+}
+
 extern "C" int disk_sv_filter_set_tile(const disk_basis *b, int H, int W, int C, int dtype, int pix) {
   if (!b) return fail(DISK_ERR_INVALID_ARG, "null basis");
   if (pix != 2 && pix != 4) return fail(DISK_ERR_INVALID_ARG, "pixels per thread must be 2 or 4");

@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
                                              _vp, _vp]),
             "disk_sv_filter_autotune": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _ip, _vp]),
             "disk_sv_filter_set_tile": (_i, [_vp, _i, _i, _i, _i, _i]),
+            "disk_sv_filter_frames": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                           ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _vp]),
             "disk_sv_filter_rotated": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp, _vp]),
             "disk_sv_filter_rotated_autotune": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp,
                                                      _vp, _ip, _vp]),
@@ -261,6 +263,34 @@ def sv_filter_rotated_autotune(basis: Basis, img, maps, angle, out=None, stream=
         basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
         _vp(maps.data_ptr()), _angle_arg(angle, H, W), chosen, _stream(stream)))
     return list(chosen)
+
+
+def sv_filter_frames(basis: Basis, h_imgs, h_maps, h_outs, stream=None):
+    """Filters frames held in host memory (CPU tensors [H, W, C], pinned for
+    the copies to overlap the filtering), maps h_maps[i] ([dims, H, W] float32
+    CPU), writing h_outs[i].  Asynchronous: synchronise the stream before
+    reading h_outs."""
+    import torch
+    n = len(h_imgs)
+    if len(h_maps) != n or len(h_outs) != n:
+        raise ValueError("h_imgs, h_maps and h_outs must have the same length")
+    if n == 0:
+        return h_outs
+    H, W, C = h_imgs[0].shape
+    dt = h_imgs[0].dtype
+    for a, m, o in zip(h_imgs, h_maps, h_outs):
+        if (a.device.type != "cpu" or o.device.type != "cpu" or m.device.type != "cpu"
+                or not a.is_contiguous() or not o.is_contiguous() or not m.is_contiguous()):
+            raise ValueError("frames, maps and outputs must be contiguous CPU tensors")
+        if tuple(a.shape) != (H, W, C) or tuple(o.shape) != (H, W, C) or a.dtype != dt or o.dtype != dt:
+            raise ValueError("all frames and outputs must share one shape and dtype")
+        if m.dtype != torch.float32 or m.numel() != basis.dims * H * W:
+            raise ValueError("maps must be float32 [dims, H, W]")
+    arr = lambda ts: (_vp * n)(*[t.data_ptr() for t in ts])
+    _check("disk_sv_filter_frames", lib().disk_sv_filter_frames(
+        basis.handle, arr(h_imgs), arr(h_outs), arr(h_maps), n, H, W, C, _dtype_code(h_imgs[0]),
+        _stream(stream)))
+    return h_outs
 
 
 def sv_filter_set_tile(basis: Basis, H: int, W: int, C: int, dtype: int, pix: int):
