@@ -245,6 +245,14 @@ int disk_sv_filter_frames(const disk_basis *basis, const void *const *h_in,
                           void *const *h_out, const float *const *h_maps, int n_frames,
                           int H, int W, int C, int dtype, void *stream);
 
+/* Device-side status of the current device: reads and clears the status
+ * word that the library's kernels set when a bounded wait gives up (a
+ * tile copy into shared memory that did not complete; the kernel then
+ * returns without computing its tile).  Synchronises `stream` first.
+ * Returns DISK_OK, or DISK_ERR_TIMEOUT if any kernel gave up since the last
+ * call (outputs written since then are then incomplete). */
+int disk_device_status(void *stream);
+
 /* Records one tile configuration (pixels per thread: 2 or 4) for every
  * layer, for this (H, W, C, dtype), in the basis handle. */
 int disk_sv_filter_set_tile(const disk_basis *basis, int H, int W, int C, int dtype,

@@ -56,6 +56,21 @@ cudaError_t scratch_alloc_raw(void **p, size_t bytes, cudaStream_t s) {
   return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
+int *device_error_word() {
+  static std::mutex mu;
+  static int *words[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!words[dev]) {
+    int *w = nullptr;
+    if (cudaMalloc(&w, sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemset(w, 0, sizeof(int)) != cudaSuccess) { cudaFree(w); return nullptr; }
+    words[dev] = w;
+  }
+  return words[dev];
+}
+
 void make_axes(int dims, const int *n_nodes, const float *node_vals, AxisNodes ax[2]) {
   int off = 0;
   for (int a = 0; a < 2; ++a) {
@@ -289,4 +304,16 @@ extern "C" int disk_basis_load(const char *path, disk_basis **out) {
   int rc = disk_basis_from_arrays((int)dims, nn, vals.data(), (int)L, (int)T, theta.data(), out);
   if (rc == DISK_ERR_INVALID_ARG) return fail(DISK_ERR_BAD_FILE, "invalid basis contents");
   return rc;
+}
+
+extern "C" int disk_device_status(void *stream) {
+  int *w = disk::device_error_word();
+  if (!w) return fail(DISK_ERR_CUDA, "device status word unavailable");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  DISK_TRY_CUDA(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, s), "read device status");
+  DISK_TRY_CUDA(cudaMemsetAsync(w, 0, sizeof(int), s), "clear device status");
+  DISK_TRY_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize(device status)");
+  if (h == DISK_ERR_TIMEOUT) return fail(DISK_ERR_TIMEOUT, "a kernel gave up a bounded wait for a tile copy");
+  return h ? fail(h, "device-side error") : DISK_OK;
 }

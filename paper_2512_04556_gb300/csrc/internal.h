@@ -48,6 +48,11 @@ inline cudaError_t scratch_alloc(T **p, size_t bytes, cudaStream_t s) {
   return scratch_alloc_raw(reinterpret_cast<void **>(p), bytes, s);
 }
 
+// Device status word of the current device (zero-initialised, one per
+// device): kernels whose bounded waits give up store DISK_ERR_TIMEOUT there;
+// disk_device_status reads and clears it.  nullptr if it cannot be allocated.
+int *device_error_word();
+
 inline int halo_of(float reach) {
   // Offsets with |o| <= reach touch pixels within ceil(reach) + 1 of the
   // output pixel (the +1 is the bilinear footprint).

@@ -392,12 +392,15 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
   P.rot = nullptr;
+  P.use_tma = 0;
+  P.err = device_error_word();
+  P.src_plane_b = P.dst_plane_b = 0;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16, mid = intermediate_kind(dtype);
   const size_t mid_bytes = kind_bytes(mid);
   for (int l = 0; l + 1 < b->L; ++l) {
-    P.halo = halo_of(b->reach[l]);
+    P.halo = P.halo_x = halo_of(b->reach[l]);
     P.region_w = kSvTileW + 2 * P.halo;
     P.src = l == 0 ? d_in : planes[l - 1];
     P.src_pitch = l == 0 ? (long long)in_pitch : (long long)(W * mid_bytes);

@@ -1,11 +1,17 @@
 // disk_sv_filter: the spatially varying cascade (Sec. 4.3 Eq. 9 + Sec. 3.2
 // Eq. 3) as one shared-memory-staged launch per layer (kernel in
 // sv_layer.cuh); disk_sv_filter_rotated: the same with every pixel's taps
-// turned by a per-pixel angle (Sec. 5.3's rotational and radial blur).  Intermediate layers live in RGBA planes of the image's
-// storage precision (FP32 or FP16) taken from the stream-ordered pool; the
-// first layer reads the caller's image and the last writes the caller's
-// output.
+// turned by a per-pixel angle (Sec. 5.3's rotational and radial blur).
+// Intermediate layers live in FP32 planar buffers (planar_* in
+// sv_common.cuh) from the library's memory pool; the first layer reads the
+// caller's image and the last writes the caller's output.  A layer that reads
+// a planar buffer has its source tile copied into shared memory by the
+// tensor-memory accelerator (one 2-D copy per plane, an mbarrier, a bounded
+// wait).
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "sv_layer.cuh"
 
@@ -26,6 +32,60 @@ __global__ void rotation_kernel(const float *__restrict__ angle, float2 *__restr
 
 namespace {
 
+// Staging geometry of layer l: halo rows above and below the tile, halo_x
+// columns left and right.  Layers after the first read a planar buffer,
+// which the tensor-memory accelerator copies when the copy's box fits its
+// 256-element limit (the (r, g) plane's box is 2 (32 + 2 halo_x) floats
+// wide); their halo_x is rounded up to a multiple of 4 pixels so that every
+// copy starts on a 16-byte boundary (tile origins are multiples of 32).
+struct LayerGeom {
+  int halo, halo_x, tma;
+};
+
+LayerGeom layer_geom(const disk_basis *b, int l, bool rot) {
+  const int h = halo_of(layer_reach(b, l, rot));
+  if (l == 0) return {h, h, 0};
+  const int hx = (h + 3) & ~3;
+  if (2 * (kSvTileW + 2 * hx) <= 256) return {h, hx, 1};
+  return {h, h, 0};
+}
+
+size_t layer_smem(const disk_basis *b, int C, int l, int pix, bool rot) {
+  const LayerGeom g = layer_geom(b, l, rot);
+  return sv_smem_bytes((size_t)(kSvTileW + 2 * g.halo_x) * (sv_tile_h(pix) + 2 * g.halo), C);
+}
+
+using EncodeTiled = PFN_cuTensorMapEncodeTiled_v12000;
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); nullptr if the driver does not provide it.
+EncodeTiled encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// 2-D FP32 tensor map of one plane: width elements per row, rows of pitch
+// bytes, box_w x box_h elements per copy, zeros outside.
+bool encode_plane(EncodeTiled fn, CUtensorMap *m, const void *base, int width, int H,
+                  long long pitch, int box_w, int box_h) {
+  const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int NP>
 int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
@@ -34,14 +94,19 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
   P.rot = nullptr;
+  P.err = device_error_word();
+  if (!P.err) return fail(DISK_ERR_CUDA, "device status word unavailable");
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
-  const int mid = intermediate_kind(dtype);
-  const size_t mid_bytes = kind_bytes(mid);
+  const int mid = PIX_PLANAR;
+  const long long mid_pitch = planar_pitch_px(W) * 8;
+  const long long mid_plane_b = (long long)planar_plane_b(H, W);
   const int L = b->L;
+  const bool rotated = d_angle != nullptr;
+  const EncodeTiled encode = encode_tiled();
   void *bufs[2] = {nullptr, nullptr};
-  const size_t plane = (size_t)H * W * mid_bytes;
+  const size_t plane = planar_bytes(H, W, C);
   const int nbuf = L >= 3 ? 2 : (L == 2 ? 1 : 0);
   for (int i = 0; i < nbuf; ++i) {
     cudaError_t e = scratch_alloc(&bufs[i], plane, s);
@@ -68,14 +133,35 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
     if (e != cudaSuccess) rc = cuda_fail(e, "launch rotation_kernel");
   }
   for (int l = 0; l < L && rc == DISK_OK; ++l) {
-    P.halo = halo_of(layer_reach(b, l, d_angle != nullptr));
-    P.region_w = kSvTileW + 2 * P.halo;
+    const LayerGeom g = layer_geom(b, l, rotated);
+    P.halo = g.halo;
+    P.halo_x = g.halo_x;
+    P.region_w = kSvTileW + 2 * g.halo_x;
     const int src = l == 0 ? user : mid;
     const int dst = l == L - 1 ? user : mid;
     P.src = l == 0 ? d_in : bufs[(l - 1) & 1];
-    P.src_pitch = l == 0 ? (long long)in_pitch : (long long)(W * mid_bytes);
+    P.src_pitch = l == 0 ? (long long)in_pitch : mid_pitch;
+    P.src_plane_b = l == 0 ? 0 : mid_plane_b;
     P.dst = l == L - 1 ? d_out : bufs[l & 1];
-    P.dst_pitch = l == L - 1 ? (long long)out_pitch : (long long)(W * mid_bytes);
+    P.dst_pitch = l == L - 1 ? (long long)out_pitch : mid_pitch;
+    P.dst_plane_b = l == L - 1 ? 0 : mid_plane_b;
+    P.use_tma = 0;
+    if (g.tma && encode) {
+      const int RW = P.region_w, RH = sv_tile_h(pix[l]) + 2 * g.halo;
+      const char *base = static_cast<const char *>(P.src);
+      const bool ok =
+          encode_plane(encode, &P.tm_a, base, 2 * W, H, mid_pitch, 2 * RW, RH) &&
+          (C == 4 ? encode_plane(encode, &P.tm_b, base + mid_plane_b, 2 * W, H, mid_pitch, 2 * RW, RH)
+                  : encode_plane(encode, &P.tm_b, base + mid_plane_b, W, H, mid_pitch / 2, RW, RH));
+      if (ok) {
+        P.use_tma = 1;
+      } else {
+        // without tensor maps the layer stages through registers, which needs
+        // no rounding of the column halo
+        P.halo_x = g.halo;
+        P.region_w = kSvTileW + 2 * g.halo;
+      }
+    }
     P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
     if (NP > 0) {
       // Tap table of this layer into the parameter block (host copy of the
@@ -101,9 +187,7 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
 }
 
 bool fits_layer(const disk_basis *b, int C, int l, int pix, bool rot) {
-  const int h = halo_of(layer_reach(b, l, rot));
-  const size_t smem = (size_t)(kSvTileW + 2 * h) * (sv_tile_h(pix) + 2 * h) * sv_stage_bytes(C);
-  return smem <= (size_t)kSvMaxSmem;
+  return layer_smem(b, C, l, pix, rot) <= (size_t)kSvMaxSmem;
 }
 
 // Per-layer tile configuration for this frame shape: the recorded one, or

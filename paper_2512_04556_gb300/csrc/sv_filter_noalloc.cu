@@ -44,6 +44,9 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
   static thread_local SvLayerParams<NP> P;
   P.maps = d_maps;
   P.rot = nullptr;
+  P.use_tma = 0;
+  P.err = device_error_word();
+  P.src_plane_b = P.dst_plane_b = 0;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
@@ -56,7 +59,7 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
                    reinterpret_cast<char *>(planes) + (size_t)H * W * mid_bytes};
   int rc = DISK_OK;
   for (int l = 0; l < L && rc == DISK_OK; ++l) {
-    P.halo = halo_of(b->reach[l]);
+    P.halo = P.halo_x = halo_of(b->reach[l]);
     P.region_w = kSvTileW + 2 * P.halo;
     const int src = l == 0 ? user : mid;
     const int dst = l == L - 1 ? user : mid;
@@ -96,7 +99,7 @@ extern "C" int disk_sv_filter_noalloc(const disk_basis *b, const void *d_in, siz
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
   for (int l = 0; l < b->L; ++l) {
     const int h = halo_of(b->reach[l]);
-    const size_t smem = (size_t)(kSvTileW + 2 * h) * (sv_tile_h(kSvDefaultPix) + 2 * h) * sv_stage_bytes(C);
+    const size_t smem = sv_smem_bytes((size_t)(kSvTileW + 2 * h) * (sv_tile_h(kSvDefaultPix) + 2 * h), C);
     if (smem > (size_t)kSvMaxSmem) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
   }
   float4 *planes = nullptr;

@@ -15,6 +15,8 @@
 // the per-pixel path.
 #pragma once
 
+#include <cuda.h>
+
 #include <type_traits>
 
 #include "sv_common.cuh"
@@ -34,19 +36,72 @@ constexpr int kSvMaxSmem = 232448;           // 227 KB opt-in shared memory per 
 // Shared-memory bytes per staged pixel: FP32 (r, g) + b, or (r, g) + (b, a).
 __host__ __device__ constexpr size_t sv_stage_bytes(int C) { return C == 4 ? 16 : 12; }
 
+// Staged region of RN pixels: the (r, g) plane, then the b / (b, a) plane at
+// a 128-byte boundary (the tensor copies' destination alignment), then the
+// copy's mbarrier (8 bytes, in a 16-byte slot).
+__host__ __device__ constexpr size_t sv_plane_b_offset(size_t RN) { return (RN * 8 + 127) & ~(size_t)127; }
+__host__ __device__ constexpr size_t sv_smem_bytes(size_t RN, int C) {
+  return ((sv_plane_b_offset(RN) + RN * (C == 4 ? 8 : 4) + 15) & ~(size_t)15) + 16;
+}
+
+// Iteration limit of the wait for a tile copy (each try_wait may also
+// suspend the thread for a while); past it the kernel records
+// DISK_ERR_TIMEOUT in *err and the block returns.
+constexpr long long kSvMaxWaitIters = 1ll << 22;
+
 template <int NP>
 struct SvLayerParams {
+  // Tensor maps of the planar source's two planes (used when use_tma).
+  alignas(64) CUtensorMap tm_a;
+  alignas(64) CUtensorMap tm_b;
   const void *src;
-  long long src_pitch;
+  long long src_pitch;   // bytes per row (plane A's rows for a planar source)
+  long long src_plane_b; // planar source: byte offset of plane B
   void *dst;
   long long dst_pitch;
+  long long dst_plane_b;
   const float *maps;
   const float2 *rot;    // [H][W] (cos, sin) of each pixel's angle, rotated variant only
   const float4 *gtaps;  // [B][T] of this layer when NP == 0: (dx, dy, w, w)
-  int H, W, C, T, halo, region_w;
+  int *err;             // device status word (DISK_ERR_TIMEOUT after a given-up wait)
+  int H, W, C, T;
+  int halo;             // rows staged above and below the tile
+  int halo_x;           // columns staged left and right (>= halo; a multiple of 4 with TMA)
+  int region_w;         // kSvTileW + 2 halo_x
+  int use_tma;          // planar source copied by the tensor-memory accelerator
   AxisNodes ax[2];
   float4 taps[NP > 0 ? NP : 1];  // [B][T] of this layer when NP > 0: (dx, dy, w, w)
 };
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+// One 2-D tile of a tensor map into shared memory, completing on mbarrier
+// bar (which expects the bytes beforehand).  x must be a multiple of 16
+// bytes' worth of elements; out-of-range elements read as zero.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];"
+      :: "r"(smem_addr(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y),
+         "r"(bar)
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of mbarrier bar; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (long long i = 0; i < kSvMaxWaitIters; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+        " selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
 
 template <int NP>
 __device__ __forceinline__ float4 node_tap(const SvLayerParams<NP> &P, int idx) {
@@ -153,13 +208,37 @@ template <int DIMS, int SRC, int DST, int NP, int CH, int PIX, bool ROT>
 __global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : 3)
 sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   constexpr int kSvPix = PIX, kSvTileH = PIX * kSvWarps;
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int halo = P.halo, RW = P.region_w, RH = kSvTileH + 2 * halo, RN = RW * RH;
+  extern __shared__ __align__(128) unsigned char sm_raw[];
+  const int halo = P.halo, hx = P.halo_x, RW = P.region_w, RH = kSvTileH + 2 * halo, RN = RW * RH;
   float2 *s_rg = reinterpret_cast<float2 *>(sm_raw);
-  float *s_b = reinterpret_cast<float *>(sm_raw + (size_t)RN * sizeof(float2));
-  float2 *s_ba = reinterpret_cast<float2 *>(sm_raw + (size_t)RN * sizeof(float2));
+  float *s_b = reinterpret_cast<float *>(sm_raw + sv_plane_b_offset(RN));
+  float2 *s_ba = reinterpret_cast<float2 *>(sm_raw + sv_plane_b_offset(RN));
+  unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(
+      sm_raw + sv_smem_bytes(RN, CH) - 16);
   const int tx0 = blockIdx.x * kSvTileW, ty0 = blockIdx.y * kSvTileH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // The tensor copies need a 128-byte aligned destination; a block whose
+  // shared window is not (never seen) records an error and does nothing.
+  const bool tma = SRC == PIX_PLANAR && P.use_tma;
+  if (tma && (smem_addr(sm_raw) & 127u) != 0) {
+    if (threadIdx.x == 0) atomicExch(P.err, DISK_ERR_UNSUPPORTED);
+    return;
+  }
+  if (tma && threadIdx.x == 0) {
+    // Both planes of the region [ty0 - halo, +RH) x [tx0 - hx, +RW) in one
+    // phase of the barrier.  x offsets: 2 (tx0 - hx) floats for the pair
+    // planes, tx0 - hx for a b plane; tx0 is a multiple of 32 and hx of 4,
+    // so both start on 16-byte boundaries as the copy requires.
+    const unsigned bar = smem_addr(s_bar);
+    const unsigned bytes = (unsigned)RN * (CH == 4 ? 16u : 12u);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes)
+                 : "memory");
+    tma_load_2d(s_rg, &P.tm_a, 2 * (tx0 - hx), ty0 - halo, bar);
+    tma_load_2d(s_b, &P.tm_b, CH == 4 ? 2 * (tx0 - hx) : tx0 - hx, ty0 - halo, bar);
+  }
 
   const int x = tx0 + lane, xc = min(x, P.W - 1);
   const long long HW = (long long)P.H * P.W;
@@ -176,29 +255,70 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     pv1[j] = DIMS == 2 ? __ldg(P.maps + HW + px) : 0.f;
     rv[j] = ROT ? __ldg(P.rot + px) : make_float2(1.f, 0.f);
   }
-  // Stage the source region, clamping coordinates to the image (Eq. 3 read
-  // with clamp-to-edge).  Each warp takes rows warp, warp + 8, ...; four of
-  // its rows are loaded before any is converted and stored, so four global
-  // loads per thread are in flight instead of one.
-  constexpr int kStageRows = 4;
-  for (int rx = lane; rx < RW; rx += 32) {
-    const int gx = min(max(tx0 - halo + rx, 0), P.W - 1);
-    for (int ry0 = warp; ry0 < RH; ry0 += kSvWarps * kStageRows) {
-      float4 v[kStageRows];
-#pragma unroll
-      for (int u = 0; u < kStageRows; ++u) {
-        const int ry = ry0 + u * kSvWarps;
-        const int gy = min(max(ty0 - halo + ry, 0), P.H - 1);
-        if (ry < RH) v[u] = load_px<SRC>(P.src, P.src_pitch, P.C, gy, gx);
+  if (tma) {
+    __syncthreads();  // the barrier is initialised before anyone waits on it
+    const bool landed = mbar_wait(smem_addr(s_bar), 0);
+    if (!__syncthreads_and(landed)) {
+      // the copy did not land in time: record it; the whole block leaves
+      // without reading the region
+      if (threadIdx.x == 0) atomicExch(P.err, DISK_ERR_TIMEOUT);
+      return;
+    }
+    // Clamp-to-edge for the parts of the region outside the image, which
+    // the copy filled with zeros: rows first (whole rows from the nearest
+    // image row, itself inside the region), then columns within each row.
+    const int y0 = ty0 - halo, x0 = tx0 - hx;
+    if (y0 < 0 || y0 + RH > P.H || x0 < 0 || x0 + RW > P.W) {
+      for (int e = threadIdx.x; e < RN; e += kSvThreads) {
+        const int ry = e / RW, rx = e - ry * RW;
+        const int gy = y0 + ry, cy = min(max(gy, 0), P.H - 1);
+        if (gy != cy) {
+          const int f = (cy - y0) * RW + rx;
+          s_rg[e] = s_rg[f];
+          if (CH == 4) s_ba[e] = s_ba[f]; else s_b[e] = s_b[f];
+        }
       }
+      __syncthreads();
+      for (int e = threadIdx.x; e < RN; e += kSvThreads) {
+        const int ry = e / RW, rx = e - ry * RW;
+        const int gx = x0 + rx, cx = min(max(gx, 0), P.W - 1);
+        if (gx != cx) {
+          const int f = ry * RW + (cx - x0);
+          s_rg[e] = s_rg[f];
+          if (CH == 4) s_ba[e] = s_ba[f]; else s_b[e] = s_b[f];
+        }
+      }
+    }
+  } else {
+    // Stage the source region, clamping coordinates to the image (Eq. 3
+    // read with clamp-to-edge).  Each warp takes rows warp, warp + 8, ...;
+    // four of its rows are loaded before any is converted and stored, so
+    // four global loads per thread are in flight instead of one.
+    constexpr int kStageRows = 4;
+    for (int rx = lane; rx < RW; rx += 32) {
+      const int gx = min(max(tx0 - hx + rx, 0), P.W - 1);
+      for (int ry0 = warp; ry0 < RH; ry0 += kSvWarps * kStageRows) {
+        float4 v[kStageRows];
 #pragma unroll
-      for (int u = 0; u < kStageRows; ++u) {
-        const int ry = ry0 + u * kSvWarps;
-        if (ry < RH) {
-          const int e = ry * RW + rx;
-          s_rg[e] = make_float2(v[u].x, v[u].y);
-          if (CH == 4) s_ba[e] = make_float2(v[u].z, v[u].w);
-          else s_b[e] = v[u].z;
+        for (int u = 0; u < kStageRows; ++u) {
+          const int ry = ry0 + u * kSvWarps;
+          const int gy = min(max(ty0 - halo + ry, 0), P.H - 1);
+          if (ry < RH) {
+            if (SRC == PIX_PLANAR)
+              v[u] = load_planar(P.src, P.src_pitch, P.src_plane_b, CH, gy, gx);
+            else
+              v[u] = load_px<SRC == PIX_PLANAR ? PIX_F32 : SRC>(P.src, P.src_pitch, P.C, gy, gx);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kStageRows; ++u) {
+          const int ry = ry0 + u * kSvWarps;
+          if (ry < RH) {
+            const int e = ry * RW + rx;
+            s_rg[e] = make_float2(v[u].x, v[u].y);
+            if (CH == 4) s_ba[e] = make_float2(v[u].z, v[u].w);
+            else s_b[e] = v[u].z;
+          }
         }
       }
     }
@@ -217,7 +337,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     c[j] = make_cell_v<DIMS>(P.ax, pv0[j], pv1[j]);
     cp[j] = cell_pairs(c[j]);
     rp[j] = {rv[j], make_float2(-rv[j].y, rv[j].x)};
-    base[j] = (warp + kSvWarps * j + halo) * RW + (lane + halo);
+    base[j] = (warp + kSvWarps * j + halo) * RW + (lane + hx);
     acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
     same = same && (c[j].n00 == c[0].n00);
   }
@@ -251,9 +371,13 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
 #pragma unroll
     for (int j = 0; j < kSvPix; ++j) {
       const int y = ty0 + warp + kSvWarps * j;
-      if (y < P.H)
-        store_px<DST>(P.dst, P.dst_pitch, P.C, y, x,
-                      make_float4(acc[j].rg.x, acc[j].rg.y, acc[j].b, acc[j].a));
+      if (y < P.H) {
+        const float4 v = make_float4(acc[j].rg.x, acc[j].rg.y, acc[j].b, acc[j].a);
+        if (DST == PIX_PLANAR)
+          store_planar(P.dst, P.dst_pitch, P.dst_plane_b, CH, y, x, v);
+        else
+          store_px<DST == PIX_PLANAR ? PIX_F32 : DST>(P.dst, P.dst_pitch, P.C, y, x, v);
+      }
     }
   }
 }
@@ -267,7 +391,7 @@ template <int DIMS, int SRC, int DST, int NP, int CH, int PIX, bool ROT>
 int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
   auto k = sv_layer_kernel<DIMS, SRC, DST, NP, CH, PIX, ROT>;
   constexpr int kSvTileH = PIX * kSvWarps;
-  const size_t smem = (size_t)P.region_w * (kSvTileH + 2 * P.halo) * sv_stage_bytes(CH);
+  const size_t smem = sv_smem_bytes((size_t)P.region_w * (kSvTileH + 2 * P.halo), CH);
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
   int dev = 0;
   cudaGetDevice(&dev);
@@ -311,6 +435,11 @@ int launch_sv_layer(int src, int dst, int C, const SvLayerParams<NP> &P, cudaStr
     DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA16, PIX_RGBA16)                                     \
     DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA16, PIX_F16)                                        \
     DISK_SV_CASE(DIMS, NP, ROT, PIX_F16, PIX_F16)                                           \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_F32, PIX_PLANAR)                                        \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_F16, PIX_PLANAR)                                        \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_PLANAR, PIX_PLANAR)                                     \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_PLANAR, PIX_F32)                                        \
+    DISK_SV_CASE(DIMS, NP, ROT, PIX_PLANAR, PIX_F16)                                        \
     return fail(DISK_ERR_INVALID_ARG, "unsupported layer storage combination");            \
   }
 

@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
                                              _vp, _vp]),
             "disk_sv_filter_autotune": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _ip, _vp]),
             "disk_sv_filter_set_tile": (_i, [_vp, _i, _i, _i, _i, _i]),
+            "disk_device_status": (_i, [_vp]),
             "disk_sv_filter_frames": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                            ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _vp]),
             "disk_sv_filter_rotated": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp, _vp]),
@@ -291,6 +292,12 @@ def sv_filter_frames(basis: Basis, h_imgs, h_maps, h_outs, stream=None):
         basis.handle, arr(h_imgs), arr(h_outs), arr(h_maps), n, H, W, C, _dtype_code(h_imgs[0]),
         _stream(stream)))
     return h_outs
+
+
+def device_status(stream=None):
+    """Raises DiskError (DISK_ERR_TIMEOUT) if a kernel gave up a bounded wait
+    since the last call; synchronises the stream."""
+    _check("disk_device_status", lib().disk_device_status(_stream(stream)))
 
 
 def sv_filter_set_tile(basis: Basis, H: int, W: int, C: int, dtype: int, pix: int):

@@ -129,3 +129,23 @@ def test_rotated_halo_limit(torch_cuda):
     with pytest.raises(disk.DiskError) as e:
         disk.sv_filter_rotated(b, t, m, torch.zeros((64, 64), device="cuda"))
     assert e.value.code == -3 or "halo" in str(e.value)
+
+
+def test_rotated_long_taps_stage_through_registers(torch_cuda):
+    """Taps up to 36 px on both axes (51 px long) give a rotated halo of 52 px:
+    the tile copy's box would exceed the tensor-memory accelerator's
+    256-element limit, so the intermediate layers stage their planar source
+    through registers."""
+    img, maps, axes, th, angle = _case(120, 140, 1, 3, 4, 1.0, 17)
+    g = np.random.default_rng(5)
+    th[..., :2] = g.uniform(-36.0, 36.0, th[..., :2].shape)
+    th[:, :, 0, 0], th[:, :, 0, 1] = 36.0, -36.0      # one diagonal tap per layer
+    got = _gpu(torch_cuda, img, maps, axes, th, angle)
+    assert rel_err(got, _oracle(img, maps, axes, th, angle)) <= TOL32
+
+
+def test_device_status_clean_after_filtering(torch_cuda):
+    from paper_2512_04556_gb300 import disk
+    img, maps, axes, th, angle = _case(64, 96, 2, 3, 6, 2.0, 23)
+    _gpu(torch_cuda, img, maps, axes, th, angle)
+    disk.device_status()
