@@ -385,11 +385,10 @@ int dispatch_theta_grad(int src, int gkind, int C, const TgParams &P, cudaStream
 
 // Recompute the forward activations I_1 .. I_{L-1} (layer inputs) into
 // planes with the forward kernels (nothing is kept from the forward call).
-template <int NP>
 int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch, int H, int W,
                           int C, int dtype, const float *d_maps, char *const *planes,
                           cudaStream_t s) {
-  static thread_local SvLayerParams<NP> P;
+  static thread_local SvLayerParams P;
   P.maps = d_maps;
   P.rot = nullptr;
   P.use_tma = 0;
@@ -407,14 +406,10 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
     P.dst = planes[l];
     P.dst_pitch = (long long)(W * mid_bytes);
     P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
-    if (NP > 0)
-      for (int k = 0; k < b->B; ++k)
-        for (int i = 0; i < b->T; ++i) {
-          const float *t = &b->theta[(((size_t)k * b->L + l) * b->T + i) * 3];
-          P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
-        }
-    const int rc = b->dims == 1 ? launch_sv_layer<1, NP, false>(l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix)
-                                : launch_sv_layer<2, NP, false>(l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix);
+    P.bt = b->B * b->T;
+    const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(kSvDefaultPix) + 2 * P.halo), C);
+    const int rc = launch_layer(b->dims, sv_taps_fit(region, P.bt), false, l == 0 ? user : mid, mid,
+                                C, P, s, kSvDefaultPix);
     if (rc) return rc;
   }
   return DISK_OK;
@@ -521,9 +516,7 @@ extern "C" int disk_sv_filter_backward(const disk_basis *b, const void *d_in, si
   float4 *gpl[2] = {reinterpret_cast<float4 *>(buf + (size_t)(L - 1) * act_plane),
                     reinterpret_cast<float4 *>(buf + (size_t)(L - 1) * act_plane + g_plane)};
   if (L > 1) {
-    rc = ((size_t)b->B * b->T <= (size_t)kSvParamTaps)
-             ? recompute_activations<kSvParamTaps>(b, d_in, in_pitch, H, W, C, dtype, d_maps, acts, s)
-             : recompute_activations<0>(b, d_in, in_pitch, H, W, C, dtype, d_maps, acts, s);
+    rc = recompute_activations(b, d_in, in_pitch, H, W, C, dtype, d_maps, acts, s);
   }
   cudaError_t e = cudaSuccess;
   if (rc == DISK_OK && d_grad_theta) {

@@ -30,6 +30,22 @@ __global__ void rotation_kernel(const float *__restrict__ angle, float2 *__restr
   }
 }
 
+int launch_layer(int dims, bool shared_taps, bool rot, int src, int dst, int C,
+                        const SvLayerParams &P, cudaStream_t s, int pix) {
+  if (dims == 1) {
+    if (rot)
+      return shared_taps ? launch_sv_layer<1, kSvTapsShared, true>(src, dst, C, P, s, pix)
+                         : launch_sv_layer<1, kSvTapsGlobal, true>(src, dst, C, P, s, pix);
+    return shared_taps ? launch_sv_layer<1, kSvTapsShared, false>(src, dst, C, P, s, pix)
+                       : launch_sv_layer<1, kSvTapsGlobal, false>(src, dst, C, P, s, pix);
+  }
+  if (rot)
+    return shared_taps ? launch_sv_layer<2, kSvTapsShared, true>(src, dst, C, P, s, pix)
+                       : launch_sv_layer<2, kSvTapsGlobal, true>(src, dst, C, P, s, pix);
+  return shared_taps ? launch_sv_layer<2, kSvTapsShared, false>(src, dst, C, P, s, pix)
+                     : launch_sv_layer<2, kSvTapsGlobal, false>(src, dst, C, P, s, pix);
+}
+
 namespace {
 
 // Staging geometry of layer l: halo rows above and below the tile, halo_x
@@ -86,12 +102,11 @@ bool encode_plane(EncodeTiled fn, CUtensorMap *m, const void *base, int width, i
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int NP>
 int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
                const float *d_angle, cudaStream_t s, const int *pix, cudaEvent_t *ev) {
   // The parameter block is large; keep it off the host stack.
-  static thread_local SvLayerParams<NP> P;
+  static thread_local SvLayerParams P;
   P.maps = d_maps;
   P.rot = nullptr;
   P.err = device_error_word();
@@ -163,22 +178,10 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
       }
     }
     P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
-    if (NP > 0) {
-      // Tap table of this layer into the parameter block (host copy of the
-      // values the device copy holds).
-      for (int k = 0; k < b->B; ++k)
-        for (int i = 0; i < b->T; ++i) {
-          const float *t = &b->theta[(((size_t)k * L + l) * b->T + i) * 3];
-          P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
-        }
-    }
+    P.bt = b->B * b->T;
     if (ev) cudaEventRecord(ev[l], s);
-    if (d_angle)
-      rc = b->dims == 1 ? launch_sv_layer<1, NP, true>(src, dst, C, P, s, pix[l])
-                        : launch_sv_layer<2, NP, true>(src, dst, C, P, s, pix[l]);
-    else
-      rc = b->dims == 1 ? launch_sv_layer<1, NP, false>(src, dst, C, P, s, pix[l])
-                        : launch_sv_layer<2, NP, false>(src, dst, C, P, s, pix[l]);
+    const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(pix[l]) + 2 * P.halo), C);
+    rc = launch_layer(b->dims, sv_taps_fit(region, P.bt), rotated, src, dst, C, P, s, pix[l]);
   }
   if (ev && rc == DISK_OK) cudaEventRecord(ev[L], s);
   for (int i = 0; i < nbuf; ++i) cudaFreeAsync(bufs[i], s);
@@ -229,11 +232,8 @@ int check_filter_args(const disk_basis *b, const void *d_in, size_t in_pitch, co
 int filter_with(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                 size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
                 const float *d_angle, cudaStream_t s, const int *pix, cudaEvent_t *ev = nullptr) {
-  if ((size_t)b->B * b->T <= (size_t)kSvParamTaps)
-    return run_filter<kSvParamTaps>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps,
-                                    d_angle, s, pix, ev);
-  return run_filter<0>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, d_angle, s,
-                       pix, ev);
+  return run_filter(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, d_angle, s, pix,
+                    ev);
 }
 
 // Times both tile configurations layer by layer (CUDA events, three passes

@@ -37,11 +37,10 @@ int planes_address(int dev, float4 **out) {
   return DISK_OK;
 }
 
-template <int NP>
 int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                 size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
                 float4 *planes, cudaStream_t s) {
-  static thread_local SvLayerParams<NP> P;
+  static thread_local SvLayerParams P;
   P.maps = d_maps;
   P.rot = nullptr;
   P.use_tma = 0;
@@ -68,15 +67,9 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
     P.dst = l == L - 1 ? d_out : bufs[l & 1];
     P.dst_pitch = l == L - 1 ? (long long)out_pitch : (long long)(W * mid_bytes);
     P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
-    if (NP > 0) {
-      for (int k = 0; k < b->B; ++k)
-        for (int i = 0; i < b->T; ++i) {
-          const float *t = &b->theta[(((size_t)k * L + l) * b->T + i) * 3];
-          P.taps[k * b->T + i] = make_float4(t[0], t[1], t[2], t[2]);
-        }
-    }
-    rc = b->dims == 1 ? launch_sv_layer<1, NP, false>(src, dst, C, P, s, kSvDefaultPix)
-                      : launch_sv_layer<2, NP, false>(src, dst, C, P, s, kSvDefaultPix);
+    P.bt = b->B * b->T;
+    const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(kSvDefaultPix) + 2 * P.halo), C);
+    rc = launch_layer(b->dims, sv_taps_fit(region, P.bt), false, src, dst, C, P, s, kSvDefaultPix);
   }
   return rc;
 }
@@ -106,8 +99,5 @@ extern "C" int disk_sv_filter_noalloc(const disk_basis *b, const void *d_in, siz
   rc = planes_address(dev, &planes);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((size_t)b->B * b->T <= (size_t)kSvParamTaps)
-    return run_noalloc<kSvParamTaps>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps,
-                                     planes, s);
-  return run_noalloc<0>(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, planes, s);
+  return run_noalloc(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, planes, s);
 }

@@ -30,7 +30,10 @@ constexpr int kSvTileW = 32, kSvThreads = 256;
 constexpr int kSvWarps = kSvThreads / 32;
 constexpr int kSvDefaultPix = 2;
 __host__ __device__ constexpr int sv_tile_h(int pix) { return pix * kSvWarps; }
-constexpr int kSvParamTaps = 1792;           // 28 KB of float4, inside the 32 KB parameter limit
+// Where a layer reads its node taps (B x T float4 (dx, dy, w, w)): a copy
+// each block makes in shared memory, or global memory through L1 when that
+// copy does not fit beside the staged region.
+enum : int { kSvTapsGlobal = 0, kSvTapsShared = 1 };
 constexpr int kSvMaxSmem = 232448;           // 227 KB opt-in shared memory per CTA
 
 // Shared-memory bytes per staged pixel: FP32 (r, g) + b, or (r, g) + (b, a).
@@ -49,7 +52,6 @@ __host__ __device__ constexpr size_t sv_smem_bytes(size_t RN, int C) {
 // DISK_ERR_TIMEOUT in *err and the block returns.
 constexpr long long kSvMaxWaitIters = 1ll << 22;
 
-template <int NP>
 struct SvLayerParams {
   // Tensor maps of the planar source's two planes (used when use_tma).
   alignas(64) CUtensorMap tm_a;
@@ -62,15 +64,15 @@ struct SvLayerParams {
   long long dst_plane_b;
   const float *maps;
   const float2 *rot;    // [H][W] (cos, sin) of each pixel's angle, rotated variant only
-  const float4 *gtaps;  // [B][T] of this layer when NP == 0: (dx, dy, w, w)
+  const float4 *gtaps;  // [B][T] taps of this layer: (dx, dy, w, w)
   int *err;             // device status word (DISK_ERR_TIMEOUT after a given-up wait)
   int H, W, C, T;
   int halo;             // rows staged above and below the tile
   int halo_x;           // columns staged left and right (>= halo; a multiple of 4 with TMA)
   int region_w;         // kSvTileW + 2 halo_x
   int use_tma;          // planar source copied by the tensor-memory accelerator
+  int bt;               // B * T taps of this layer
   AxisNodes ax[2];
-  float4 taps[NP > 0 ? NP : 1];  // [B][T] of this layer when NP > 0: (dx, dy, w, w)
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
@@ -101,12 +103,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
     if (ok) return true;
   }
   return false;
-}
-
-template <int NP>
-__device__ __forceinline__ float4 node_tap(const SvLayerParams<NP> &P, int idx) {
-  if (NP > 0) return P.taps[idx];
-  return __ldg(P.gtaps + idx);
 }
 
 // Pixel weights of Eq. 9 broadcast into FP32 pairs for the packed
@@ -204,9 +200,9 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   add_corner<CH>(st, e + RW + 1, w11, acc);
 }
 
-template <int DIMS, int SRC, int DST, int NP, int CH, int PIX, bool ROT>
+template <int DIMS, int SRC, int DST, int TAPS, int CH, int PIX, bool ROT>
 __global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : 3)
-sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
+sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   constexpr int kSvPix = PIX, kSvTileH = PIX * kSvWarps;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   const int halo = P.halo, hx = P.halo_x, RW = P.region_w, RH = kSvTileH + 2 * halo, RN = RW * RH;
@@ -215,6 +211,15 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
   float2 *s_ba = reinterpret_cast<float2 *>(sm_raw + sv_plane_b_offset(RN));
   unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(
       sm_raw + sv_smem_bytes(RN, CH) - 16);
+  // This layer's node taps, copied into shared memory by every block (read
+  // before the first barrier below); a warp's threads mostly fetch the same
+  // tap, a broadcast.
+  float4 *s_taps = reinterpret_cast<float4 *>(sm_raw + sv_smem_bytes(RN, CH));
+  if (TAPS == kSvTapsShared)
+    for (int i = threadIdx.x; i < P.bt; i += kSvThreads) s_taps[i] = __ldg(P.gtaps + i);
+  auto ntap = [&](int idx) -> float4 {
+    return TAPS == kSvTapsShared ? s_taps[idx] : __ldg(P.gtaps + idx);
+  };
   const int tx0 = blockIdx.x * kSvTileW, ty0 = blockIdx.y * kSvTileH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // The tensor copies need a 128-byte aligned destination; a block whose
@@ -346,9 +351,9 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
     const int b00 = c[0].n00 * T, b10 = c[0].n10 * T, b01 = c[0].n01 * T, b11 = c[0].n11 * T;
 #pragma unroll 2
     for (int i = 0; i < T; ++i) {
-      const float4 q00 = node_tap(P, b00 + i), q10 = node_tap(P, b10 + i);
-      const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
-      const float4 q11 = DIMS == 2 ? node_tap(P, b11 + i) : q10;
+      const float4 q00 = ntap(b00 + i), q10 = ntap(b10 + i);
+      const float4 q01 = DIMS == 2 ? ntap(b01 + i) : q00;
+      const float4 q11 = DIMS == 2 ? ntap(b11 + i) : q10;
 #pragma unroll
       for (int j = 0; j < kSvPix; ++j)
         sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
@@ -360,9 +365,9 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
       const int b00 = c[j].n00 * T, b10 = c[j].n10 * T, b01 = c[j].n01 * T, b11 = c[j].n11 * T;
 #pragma unroll 1
       for (int i = 0; i < T; ++i) {
-        const float4 q00 = node_tap(P, b00 + i), q10 = node_tap(P, b10 + i);
-        const float4 q01 = DIMS == 2 ? node_tap(P, b01 + i) : q00;
-        const float4 q11 = DIMS == 2 ? node_tap(P, b11 + i) : q10;
+        const float4 q00 = ntap(b00 + i), q10 = ntap(b10 + i);
+        const float4 q01 = DIMS == 2 ? ntap(b01 + i) : q00;
+        const float4 q11 = DIMS == 2 ? ntap(b11 + i) : q10;
         sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
       }
     }
@@ -387,11 +392,12 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams<NP> P) {
 __global__ void rotation_kernel(const float *__restrict__ angle, float2 *__restrict__ rot,
                                 long long n);
 
-template <int DIMS, int SRC, int DST, int NP, int CH, int PIX, bool ROT>
-int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
-  auto k = sv_layer_kernel<DIMS, SRC, DST, NP, CH, PIX, ROT>;
+template <int DIMS, int SRC, int DST, int TAPS, int CH, int PIX, bool ROT>
+int launch_sv_layer_t(const SvLayerParams &P, cudaStream_t s) {
+  auto k = sv_layer_kernel<DIMS, SRC, DST, TAPS, CH, PIX, ROT>;
   constexpr int kSvTileH = PIX * kSvWarps;
-  const size_t smem = sv_smem_bytes((size_t)P.region_w * (kSvTileH + 2 * P.halo), CH);
+  const size_t smem = sv_smem_bytes((size_t)P.region_w * (kSvTileH + 2 * P.halo), CH) +
+                      (TAPS == kSvTapsShared ? (size_t)P.bt * sizeof(float4) : 0);
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
   int dev = 0;
   cudaGetDevice(&dev);
@@ -407,39 +413,50 @@ int launch_sv_layer_t(const SvLayerParams<NP> &P, cudaStream_t s) {
 }
 
 // Storage combination of one layer: (source kind, destination kind), tile
-// configuration pix (2 or 4 pixels per thread); ROT selects the rotated
-// variant (P.angle set).
-template <int DIMS, int NP, bool ROT>
-int launch_sv_layer(int src, int dst, int C, const SvLayerParams<NP> &P, cudaStream_t s, int pix);
+// configuration pix (2 or 4 pixels per thread); TAPS where the node taps are
+// read; ROT selects the rotated variant (P.rot set).
+template <int DIMS, int TAPS, bool ROT>
+int launch_sv_layer(int src, int dst, int C, const SvLayerParams &P, cudaStream_t s, int pix);
 
-#define DISK_SV_CASE(DIMS, NP, ROT, S, D)                                                   \
+// Whether a layer's taps (bt float4) fit in shared memory beside a staged
+// region of region_smem bytes.
+inline bool sv_taps_fit(size_t region_smem, int bt) {
+  return region_smem + (size_t)bt * sizeof(float4) <= (size_t)kSvMaxSmem;
+}
+
+// One layer of any variant: dims 1 or 2, taps in shared memory or global
+// (defined with the filter's host code).
+int launch_layer(int dims, bool shared_taps, bool rot, int src, int dst, int C,
+                 const SvLayerParams &P, cudaStream_t s, int pix);
+
+#define DISK_SV_CASE(DIMS, TAPS, ROT, S, D)                                                 \
   if (src == S && dst == D) {                                                               \
     if (pix == 4)                                                                           \
-      return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4, 4, ROT>(P, s)                        \
-                : launch_sv_layer_t<DIMS, S, D, NP, 3, 4, ROT>(P, s);                       \
-    return c4 ? launch_sv_layer_t<DIMS, S, D, NP, 4, 2, ROT>(P, s)                          \
-              : launch_sv_layer_t<DIMS, S, D, NP, 3, 2, ROT>(P, s);                         \
+      return c4 ? launch_sv_layer_t<DIMS, S, D, TAPS, 4, 4, ROT>(P, s)                      \
+                : launch_sv_layer_t<DIMS, S, D, TAPS, 3, 4, ROT>(P, s);                     \
+    return c4 ? launch_sv_layer_t<DIMS, S, D, TAPS, 4, 2, ROT>(P, s)                        \
+              : launch_sv_layer_t<DIMS, S, D, TAPS, 3, 2, ROT>(P, s);                       \
   }
 
 // FP32 images: FP32 planes; FP16 images: FP16 planes (see intermediate_kind).
-#define DISK_SV_INSTANTIATE(DIMS, NP, ROT)                                                  \
+#define DISK_SV_INSTANTIATE(DIMS, TAPS, ROT)                                                \
   template <>                                                                               \
-  int launch_sv_layer<DIMS, NP, ROT>(int src, int dst, int C, const SvLayerParams<NP> &P,     \
-                                     cudaStream_t s, int pix) {                             \
+  int launch_sv_layer<DIMS, TAPS, ROT>(int src, int dst, int C, const SvLayerParams &P,       \
+                                       cudaStream_t s, int pix) {                           \
     const bool c4 = C == 4;                                                                 \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_F32, PIX_RGBA32)                                        \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA32, PIX_RGBA32)                                     \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA32, PIX_F32)                                        \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_F32, PIX_F32)                                           \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_F16, PIX_RGBA16)                                        \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA16, PIX_RGBA16)                                     \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_RGBA16, PIX_F16)                                        \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_F16, PIX_F16)                                           \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_F32, PIX_PLANAR)                                        \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_F16, PIX_PLANAR)                                        \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_PLANAR, PIX_PLANAR)                                     \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_PLANAR, PIX_F32)                                        \
-    DISK_SV_CASE(DIMS, NP, ROT, PIX_PLANAR, PIX_F16)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F32, PIX_RGBA32)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA32, PIX_RGBA32)                                     \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA32, PIX_F32)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F32, PIX_F32)                                           \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_RGBA16)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA16, PIX_RGBA16)                                     \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA16, PIX_F16)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_F16)                                           \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F32, PIX_PLANAR)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_PLANAR)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_PLANAR, PIX_PLANAR)                                     \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_PLANAR, PIX_F32)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_PLANAR, PIX_F16)                                        \
     return fail(DISK_ERR_INVALID_ARG, "unsupported layer storage combination");            \
   }
 

@@ -2,6 +2,6 @@
 #include "sv_layer.cuh"
 
 namespace disk {
-DISK_SV_INSTANTIATE(1, kSvParamTaps, false)
-DISK_SV_INSTANTIATE(1, 0, false)
+DISK_SV_INSTANTIATE(1, kSvTapsShared, false)
+DISK_SV_INSTANTIATE(1, kSvTapsGlobal, false)
 }  // namespace disk

@@ -2,6 +2,6 @@
 #include "sv_layer.cuh"
 
 namespace disk {
-DISK_SV_INSTANTIATE(2, kSvParamTaps, false)
-DISK_SV_INSTANTIATE(2, 0, false)
+DISK_SV_INSTANTIATE(2, kSvTapsShared, false)
+DISK_SV_INSTANTIATE(2, kSvTapsGlobal, false)
 }  // namespace disk

@@ -2,6 +2,6 @@
 #include "sv_layer.cuh"
 
 namespace disk {
-DISK_SV_INSTANTIATE(1, kSvParamTaps, true)
-DISK_SV_INSTANTIATE(1, 0, true)
+DISK_SV_INSTANTIATE(1, kSvTapsShared, true)
+DISK_SV_INSTANTIATE(1, kSvTapsGlobal, true)
 }  // namespace disk

@@ -2,6 +2,6 @@
 #include "sv_layer.cuh"
 
 namespace disk {
-DISK_SV_INSTANTIATE(2, kSvParamTaps, true)
-DISK_SV_INSTANTIATE(2, 0, true)
+DISK_SV_INSTANTIATE(2, kSvTapsShared, true)
+DISK_SV_INSTANTIATE(2, kSvTapsGlobal, true)
 }  // namespace disk
