@@ -181,7 +181,8 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
     P.bt = b->B * b->T;
     if (ev) cudaEventRecord(ev[l], s);
     const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(pix[l]) + 2 * P.halo), C);
-    rc = launch_layer(b->dims, sv_taps_fit(region, P.bt), rotated, src, dst, C, P, s, pix[l]);
+    P.tap_cap = sv_tap_cap(b->dims, b->n_nodes[1], b->B, b->T, region);
+    rc = launch_layer(b->dims, P.tap_cap > 0, rotated, src, dst, C, P, s, pix[l]);
   }
   if (ev && rc == DISK_OK) cudaEventRecord(ev[L], s);
   for (int i = 0; i < nbuf; ++i) cudaFreeAsync(bufs[i], s);

@@ -69,7 +69,8 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
     P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
     P.bt = b->B * b->T;
     const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(kSvDefaultPix) + 2 * P.halo), C);
-    rc = launch_layer(b->dims, sv_taps_fit(region, P.bt), false, src, dst, C, P, s, kSvDefaultPix);
+    P.tap_cap = sv_tap_cap(b->dims, b->n_nodes[1], b->B, b->T, region);
+    rc = launch_layer(b->dims, P.tap_cap > 0, false, src, dst, C, P, s, kSvDefaultPix);
   }
   return rc;
 }

@@ -72,6 +72,7 @@ struct SvLayerParams {
   int region_w;         // kSvTileW + 2 halo_x
   int use_tma;          // planar source copied by the tensor-memory accelerator
   int bt;               // B * T taps of this layer
+  int tap_cap;          // nodes whose taps a block may copy into shared memory
   AxisNodes ax[2];
 };
 
@@ -211,15 +212,11 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   float2 *s_ba = reinterpret_cast<float2 *>(sm_raw + sv_plane_b_offset(RN));
   unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(
       sm_raw + sv_smem_bytes(RN, CH) - 16);
-  // This layer's node taps, copied into shared memory by every block (read
-  // before the first barrier below); a warp's threads mostly fetch the same
-  // tap, a broadcast.
+  // The node taps the block needs, copied into shared memory after the
+  // block's node range is known (see below); a warp's threads mostly fetch
+  // the same tap, a broadcast.
   float4 *s_taps = reinterpret_cast<float4 *>(sm_raw + sv_smem_bytes(RN, CH));
-  if (TAPS == kSvTapsShared)
-    for (int i = threadIdx.x; i < P.bt; i += kSvThreads) s_taps[i] = __ldg(P.gtaps + i);
-  auto ntap = [&](int idx) -> float4 {
-    return TAPS == kSvTapsShared ? s_taps[idx] : __ldg(P.gtaps + idx);
-  };
+  unsigned *s_range = reinterpret_cast<unsigned *>(s_bar + 1);  // lowest, highest node
   const int tx0 = blockIdx.x * kSvTileW, ty0 = blockIdx.y * kSvTileH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // The tensor copies need a 128-byte aligned destination; a block whose
@@ -228,6 +225,10 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   if (tma && (smem_addr(sm_raw) & 127u) != 0) {
     if (threadIdx.x == 0) atomicExch(P.err, DISK_ERR_UNSUPPORTED);
     return;
+  }
+  if (TAPS == kSvTapsShared && threadIdx.x == 0) {
+    s_range[0] = 0xffffffffu;
+    s_range[1] = 0u;
   }
   if (tma && threadIdx.x == 0) {
     // Both planes of the region [ty0 - halo, +RH) x [tx0 - hx, +RW) in one
@@ -248,20 +249,56 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   const int x = tx0 + lane, xc = min(x, P.W - 1);
   const long long HW = (long long)P.H * P.W;
   const int T = P.T;
-  // This thread's map values (and rotations), loaded before the staging so
-  // their latency overlaps its loads; the cells are formed after it.
-  float pv0[kSvPix], pv1[kSvPix];
-  float2 rv[kSvPix];
+  // This thread's pixels: Eq. 9 cells from the maps (and rotations), formed
+  // while the tile copy is in flight.
+  Cell c[kSvPix];
+  CellPairs cp[kSvPix];
+  RotPairs rp[kSvPix];
+  int base[kSvPix];
+  Acc acc[kSvPix];
+  bool same = true;
 #pragma unroll
   for (int j = 0; j < kSvPix; ++j) {
     const int yc = min(ty0 + warp + kSvWarps * j, P.H - 1);
     const long long px = (long long)yc * P.W + xc;
-    pv0[j] = __ldg(P.maps + px);
-    pv1[j] = DIMS == 2 ? __ldg(P.maps + HW + px) : 0.f;
-    rv[j] = ROT ? __ldg(P.rot + px) : make_float2(1.f, 0.f);
+    c[j] = make_cell_v<DIMS>(P.ax, __ldg(P.maps + px), DIMS == 2 ? __ldg(P.maps + HW + px) : 0.f);
+    cp[j] = cell_pairs(c[j]);
+    const float2 r = ROT ? __ldg(P.rot + px) : make_float2(1.f, 0.f);
+    rp[j] = {r, make_float2(-r.y, r.x)};
+    base[j] = (warp + kSvWarps * j + halo) * RW + (lane + hx);
+    acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
+    same = same && (c[j].n00 == c[0].n00);
+  }
+  __syncthreads();  // the copy's mbarrier and the range slots are initialised
+  // Node range of the block (lowest n00, highest n11 over its pixels); when
+  // it spans at most tap_cap nodes their taps are copied into shared memory,
+  // else the block reads taps from global memory.  tap_base: index of the
+  // first copied tap.
+  bool shared_taps = false;
+  int tap_base = 0;
+  if (TAPS == kSvTapsShared) {
+    unsigned lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+    for (int j = 0; j < kSvPix; ++j) {
+      lo = min(lo, (unsigned)c[j].n00);
+      hi = max(hi, (unsigned)c[j].n11);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+      atomicMin(&s_range[0], lo);
+      atomicMax(&s_range[1], hi);
+    }
+    __syncthreads();
+    const int nlo = (int)s_range[0], nhi = (int)s_range[1];
+    shared_taps = nhi - nlo < P.tap_cap;
+    if (shared_taps) {
+      tap_base = nlo * T;
+      const int n = (nhi - nlo + 1) * T;
+      for (int i = threadIdx.x; i < n; i += kSvThreads) s_taps[i] = __ldg(P.gtaps + tap_base + i);
+    }
   }
   if (tma) {
-    __syncthreads();  // the barrier is initialised before anyone waits on it
     const bool landed = mbar_wait(smem_addr(s_bar), 0);
     if (!__syncthreads_and(landed)) {
       // the copy did not land in time: record it; the whole block leaves
@@ -331,46 +368,41 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   __syncthreads();
   const Staged st{s_rg, s_b, s_ba};
 
-  Cell c[kSvPix];
-  CellPairs cp[kSvPix];
-  RotPairs rp[kSvPix];
-  int base[kSvPix];
-  Acc acc[kSvPix];
-  bool same = true;
-#pragma unroll
-  for (int j = 0; j < kSvPix; ++j) {
-    c[j] = make_cell_v<DIMS>(P.ax, pv0[j], pv1[j]);
-    cp[j] = cell_pairs(c[j]);
-    rp[j] = {rv[j], make_float2(-rv[j].y, rv[j].x)};
-    base[j] = (warp + kSvWarps * j + halo) * RW + (lane + hx);
-    acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
-    same = same && (c[j].n00 == c[0].n00);
-  }
-  if (__all_sync(0xffffffffu, same)) {
-    // each thread's pixels share a cell: one node fetch per tap serves them
-    const int b00 = c[0].n00 * T, b10 = c[0].n10 * T, b01 = c[0].n01 * T, b11 = c[0].n11 * T;
+  // The tap loops, once per source of node taps (the choice is uniform over
+  // the block).
+  auto run_taps = [&](auto fetch) {
+    if (__all_sync(0xffffffffu, same)) {
+      // each thread's pixels share a cell: one node fetch per tap serves them
+      const int b00 = c[0].n00 * T, b10 = c[0].n10 * T, b01 = c[0].n01 * T, b11 = c[0].n11 * T;
 #pragma unroll 2
-    for (int i = 0; i < T; ++i) {
-      const float4 q00 = ntap(b00 + i), q10 = ntap(b10 + i);
-      const float4 q01 = DIMS == 2 ? ntap(b01 + i) : q00;
-      const float4 q11 = DIMS == 2 ? ntap(b11 + i) : q10;
-#pragma unroll
-      for (int j = 0; j < kSvPix; ++j)
-        sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
-    }
-  } else {
-    // unrolled so the per-pixel arrays stay in registers
-#pragma unroll
-    for (int j = 0; j < kSvPix; ++j) {
-      const int b00 = c[j].n00 * T, b10 = c[j].n10 * T, b01 = c[j].n01 * T, b11 = c[j].n11 * T;
-#pragma unroll 1
       for (int i = 0; i < T; ++i) {
-        const float4 q00 = ntap(b00 + i), q10 = ntap(b10 + i);
-        const float4 q01 = DIMS == 2 ? ntap(b01 + i) : q00;
-        const float4 q11 = DIMS == 2 ? ntap(b11 + i) : q10;
-        sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
+        const float4 q00 = fetch(b00 + i), q10 = fetch(b10 + i);
+        const float4 q01 = DIMS == 2 ? fetch(b01 + i) : q00;
+        const float4 q11 = DIMS == 2 ? fetch(b11 + i) : q10;
+#pragma unroll
+        for (int j = 0; j < kSvPix; ++j)
+          sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
+      }
+    } else {
+      // unrolled so the per-pixel arrays stay in registers
+#pragma unroll
+      for (int j = 0; j < kSvPix; ++j) {
+        const int b00 = c[j].n00 * T, b10 = c[j].n10 * T, b01 = c[j].n01 * T, b11 = c[j].n11 * T;
+#pragma unroll 1
+        for (int i = 0; i < T; ++i) {
+          const float4 q00 = fetch(b00 + i), q10 = fetch(b10 + i);
+          const float4 q01 = DIMS == 2 ? fetch(b01 + i) : q00;
+          const float4 q11 = DIMS == 2 ? fetch(b11 + i) : q10;
+          sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
+        }
       }
     }
+  };
+  if (TAPS == kSvTapsShared && shared_taps) {
+    const float4 *t = s_taps - tap_base;
+    run_taps([&](int idx) { return t[idx]; });
+  } else {
+    run_taps([&](int idx) { return __ldg(P.gtaps + idx); });
   }
   if (x < P.W) {
 #pragma unroll
@@ -397,7 +429,7 @@ int launch_sv_layer_t(const SvLayerParams &P, cudaStream_t s) {
   auto k = sv_layer_kernel<DIMS, SRC, DST, TAPS, CH, PIX, ROT>;
   constexpr int kSvTileH = PIX * kSvWarps;
   const size_t smem = sv_smem_bytes((size_t)P.region_w * (kSvTileH + 2 * P.halo), CH) +
-                      (TAPS == kSvTapsShared ? (size_t)P.bt * sizeof(float4) : 0);
+                      (TAPS == kSvTapsShared ? (size_t)P.tap_cap * P.T * sizeof(float4) : 0);
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
   int dev = 0;
   cudaGetDevice(&dev);
@@ -418,10 +450,15 @@ int launch_sv_layer_t(const SvLayerParams &P, cudaStream_t s) {
 template <int DIMS, int TAPS, bool ROT>
 int launch_sv_layer(int src, int dst, int C, const SvLayerParams &P, cudaStream_t s, int pix);
 
-// Whether a layer's taps (bt float4) fit in shared memory beside a staged
-// region of region_smem bytes.
-inline bool sv_taps_fit(size_t region_smem, int bt) {
-  return region_smem + (size_t)bt * sizeof(float4) <= (size_t)kSvMaxSmem;
+// How many nodes' taps a block copies into shared memory (0: the layer reads
+// them from global memory).  A block needs the nodes between the lowest and
+// the highest index of its pixels' cells; with smooth maps a tile spans one
+// or two cells per axis, i.e. at most 2 n1 + 4 consecutive indices of a 2-D
+// basis (n1 nodes on axis 1).  Small tables are copied whole.
+inline int sv_tap_cap(int dims, int n1, int B, int T, size_t region_smem) {
+  int cap = (size_t)B * T * sizeof(float4) <= 8192 ? B : (dims == 1 ? 8 : 2 * n1 + 4);
+  cap = cap < B ? cap : B;
+  return region_smem + (size_t)cap * T * sizeof(float4) <= (size_t)kSvMaxSmem ? cap : 0;
 }
 
 // One layer of any variant: dims 1 or 2, taps in shared memory or global
