@@ -249,55 +249,25 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   const int x = tx0 + lane, xc = min(x, P.W - 1);
   const long long HW = (long long)P.H * P.W;
   const int T = P.T;
-  // This thread's pixels: Eq. 9 cells from the maps (and rotations), formed
-  // while the tile copy is in flight.
-  Cell c[kSvPix];
-  CellPairs cp[kSvPix];
-  RotPairs rp[kSvPix];
-  int base[kSvPix];
-  Acc acc[kSvPix];
-  bool same = true;
+  // A table small enough for every block to hold whole is copied now,
+  // overlapping the tile copy; larger ones are copied per node range below.
+  const bool whole = TAPS == kSvTapsShared && P.tap_cap * T >= P.bt;
+  if (whole)
+    for (int i = threadIdx.x; i < P.bt; i += kSvThreads) s_taps[i] = __ldg(P.gtaps + i);
+  // This thread's map values (and rotations), loaded before the staging so
+  // their latency overlaps it; the cells are formed after it.
+  float pv0[kSvPix], pv1[kSvPix];
+  float2 rv[kSvPix];
 #pragma unroll
   for (int j = 0; j < kSvPix; ++j) {
     const int yc = min(ty0 + warp + kSvWarps * j, P.H - 1);
     const long long px = (long long)yc * P.W + xc;
-    c[j] = make_cell_v<DIMS>(P.ax, __ldg(P.maps + px), DIMS == 2 ? __ldg(P.maps + HW + px) : 0.f);
-    cp[j] = cell_pairs(c[j]);
-    const float2 r = ROT ? __ldg(P.rot + px) : make_float2(1.f, 0.f);
-    rp[j] = {r, make_float2(-r.y, r.x)};
-    base[j] = (warp + kSvWarps * j + halo) * RW + (lane + hx);
-    acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
-    same = same && (c[j].n00 == c[0].n00);
+    pv0[j] = __ldg(P.maps + px);
+    pv1[j] = DIMS == 2 ? __ldg(P.maps + HW + px) : 0.f;
+    rv[j] = ROT ? __ldg(P.rot + px) : make_float2(1.f, 0.f);
   }
-  __syncthreads();  // the copy's mbarrier and the range slots are initialised
-  // Node range of the block (lowest n00, highest n11 over its pixels); when
-  // it spans at most tap_cap nodes their taps are copied into shared memory,
-  // else the block reads taps from global memory.  tap_base: index of the
-  // first copied tap.
-  bool shared_taps = false;
-  int tap_base = 0;
-  if (TAPS == kSvTapsShared) {
-    unsigned lo = 0xffffffffu, hi = 0u;
-#pragma unroll
-    for (int j = 0; j < kSvPix; ++j) {
-      lo = min(lo, (unsigned)c[j].n00);
-      hi = max(hi, (unsigned)c[j].n11);
-    }
-    lo = __reduce_min_sync(0xffffffffu, lo);
-    hi = __reduce_max_sync(0xffffffffu, hi);
-    if (lane == 0) {
-      atomicMin(&s_range[0], lo);
-      atomicMax(&s_range[1], hi);
-    }
-    __syncthreads();
-    const int nlo = (int)s_range[0], nhi = (int)s_range[1];
-    shared_taps = nhi - nlo < P.tap_cap;
-    if (shared_taps) {
-      tap_base = nlo * T;
-      const int n = (nhi - nlo + 1) * T;
-      for (int i = threadIdx.x; i < n; i += kSvThreads) s_taps[i] = __ldg(P.gtaps + tap_base + i);
-    }
-  }
+  const bool ranged = TAPS == kSvTapsShared && !whole;
+  if (tma || ranged) __syncthreads();  // the copy's mbarrier and the range slots are initialised
   if (tma) {
     const bool landed = mbar_wait(smem_addr(s_bar), 0);
     if (!__syncthreads_and(landed)) {
@@ -363,6 +333,49 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
           }
         }
       }
+    }
+  }
+  Cell c[kSvPix];
+  CellPairs cp[kSvPix];
+  RotPairs rp[kSvPix];
+  int base[kSvPix];
+  Acc acc[kSvPix];
+  bool same = true;
+#pragma unroll
+  for (int j = 0; j < kSvPix; ++j) {
+    c[j] = make_cell_v<DIMS>(P.ax, pv0[j], pv1[j]);
+    cp[j] = cell_pairs(c[j]);
+    rp[j] = {rv[j], make_float2(-rv[j].y, rv[j].x)};
+    base[j] = (warp + kSvWarps * j + halo) * RW + (lane + hx);
+    acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
+    same = same && (c[j].n00 == c[0].n00);
+  }
+  // Node range of the block (lowest n00, highest n11 over its pixels); when
+  // it spans at most tap_cap nodes their taps are copied into shared memory,
+  // else the block reads taps from global memory.  tap_base: index of the
+  // first copied tap.
+  bool shared_taps = whole;
+  int tap_base = 0;
+  if (ranged) {
+    unsigned lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+    for (int j = 0; j < kSvPix; ++j) {
+      lo = min(lo, (unsigned)c[j].n00);
+      hi = max(hi, (unsigned)c[j].n11);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+      atomicMin(&s_range[0], lo);
+      atomicMax(&s_range[1], hi);
+    }
+    __syncthreads();
+    const int nlo = (int)s_range[0], nhi = (int)s_range[1];
+    shared_taps = nhi - nlo < P.tap_cap;
+    if (shared_taps) {
+      tap_base = nlo * T;
+      const int n = (nhi - nlo + 1) * T;
+      for (int i = threadIdx.x; i < n; i += kSvThreads) s_taps[i] = __ldg(P.gtaps + tap_base + i);
     }
   }
   __syncthreads();
