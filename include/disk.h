@@ -326,14 +326,21 @@ int disk_fit(const float *d_targets, const int *sizes, int batch, int L, int T,
              float *d_loss_hist, void *stream);
 
 /* Launch-configuration autotuner of disk_fit: times the persistent fit kernel
- * with 256, 512 and 1024 threads per target (a few steps each, from the
- * radial initialisation) on this batch, and records the fastest for every
- * later disk_fit with the same L, T and largest target size (in 32-pixel
- * buckets); without a recorded choice disk_fit uses 512.  Synchronises the
- * stream (do not call while capturing a graph).  *chosen_threads (may be
- * NULL) receives the choice. */
+ * in each built configuration -- 256, 512 or 1024 threads per CTA, and one
+ * CTA or a thread-block cluster of 2 or 4 CTAs (on as many SMs) per target --
+ * for a few steps each from the radial initialisation on this batch, and
+ * records the fastest for every later disk_fit with the same L, T and largest
+ * target size (in 32-pixel buckets); without a recorded choice disk_fit uses
+ * 512 threads, one CTA per target.  Synchronises the stream (do not call
+ * while capturing a graph).  *chosen_config (may be NULL) receives the
+ * choice as threads * 16 + CTAs per target. */
 int disk_fit_autotune(const float *d_targets, const int *sizes, int batch, int L,
-                      int T, int loss, float eps, int *chosen_threads, void *stream);
+                      int T, int loss, float eps, int *chosen_config, void *stream);
+
+/* Records a launch configuration (threads * 16 + CTAs per target, one of
+ * those disk_fit_autotune tries) for disk_fit calls with this L, T and
+ * largest target size kmax.  DISK_ERR_INVALID_ARG for any other value. */
+int disk_fit_set_config(int L, int T, int kmax, int config);
 
 /* One evaluation of the fit objective and its gradient (the hand-written
  * backward of the cascade: d/dw, d/ddx, d/ddy of every tap, through the

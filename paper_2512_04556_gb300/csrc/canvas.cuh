@@ -1,7 +1,9 @@
 // Device building blocks for shift-invariant complexes on a zero-padded
 // square canvas (impulse synthesis, Sec. 4.4 Eq. 10, and its adjoint for the
 // fit).  A canvas of half-width R is a dense (2R+1)^2 float plane centred on
-// c = (R, R).  All routines are executed by every thread of one CTA.
+// c = (R, R).  All routines are executed by every thread of one CTA, or of
+// every CTA of a cluster that shares the canvas (tid, nthr: the thread's
+// index among, and the number of, the threads that split the work).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,11 +20,12 @@ struct LayerExtent {
 };
 
 // Zero the square frame b_in < max(|dx|,|dy|) <= b_out of a canvas.
-__device__ __forceinline__ void zero_frame(float *plane, int R, int b_in, int b_out) {
+__device__ __forceinline__ void zero_frame(float *plane, int R, int b_in, int b_out,
+                                           int tid = threadIdx.x, int nthr = blockDim.x) {
   b_out = min(b_out, R);
   if (b_out <= b_in) return;
   const int side = 2 * b_out + 1, N = 2 * R + 1;
-  for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
+  for (int j = tid; j < side * side; j += nthr) {
     const int v = j / side - b_out, u = j % side - b_out;
     if (max(abs(u), abs(v)) > b_in) plane[(R + v) * N + (R + u)] = 0.f;
   }
@@ -44,9 +47,10 @@ __device__ __forceinline__ int split_floor(float d, float &f) {
 // as ceil(reach) + 1.  sign = -1 applies the taps at -o (the adjoint of a
 // layer on a zero-bounded canvas, by the symmetry of the bilinear tent).
 __device__ __forceinline__ void canvas_layer(const float *src, float *dst, int R, int b,
-                                             const float4 *taps, int T, int halo, float sign) {
+                                             const float4 *taps, int T, int halo, float sign,
+                                             int tid = threadIdx.x, int nthr = blockDim.x) {
   const int side = 2 * b + 1, N = 2 * R + 1;
-  for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
+  for (int j = tid; j < side * side; j += nthr) {
     const int v = j / side - b, u = j % side - b;
     const float *base = src + (R + v) * N + (R + u);
     float acc = 0.f;

@@ -2,8 +2,13 @@
 // Sec. 4.2 Eq. 7, Sec. 4.4 Eq. 10-11, schedule of Sec. 5.1), batched over
 // targets of uneven size in one persistent launch.
 //
-// One CTA owns one target for all steps (targets ordered largest first, so
-// the block scheduler runs them longest-processing-time first).  Per step:
+// One CTA -- or one thread-block cluster of CL CTAs on CL SMs -- owns one
+// target for all steps (targets ordered largest first, so the block
+// scheduler runs them longest-processing-time first).  In a cluster every
+// canvas sweep is split over the cluster's threads, the canvases stay in
+// global memory, cluster barriers order the sweeps, and the loss and tap
+// gradients are summed across the CTAs through distributed shared memory in a
+// fixed order, so every CTA applies the same Adam update.  Per step:
 //   forward   impulse on a zero-padded canvas, L shift-invariant layers, each
 //             computed only on its support box S_l = H_1 + ... + H_l, with
 //             H_l = ceil(max |o_l|) + 1 from the current taps;
@@ -26,6 +31,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "canvas.cuh"
 
 namespace disk {
@@ -34,6 +41,7 @@ namespace {
 constexpr int kFitThreads = 512;      // init kernel and default fit CTA size
 constexpr int kFitWarps = kFitThreads / 32;
 constexpr int kFitMaxWarps = 32;      // largest fit CTA: 1024 threads
+constexpr int kFitMaxCluster = 4;     // CTAs per target
 
 struct FitMeta {
   long long tgt_off;     // floats into the packed targets
@@ -233,7 +241,38 @@ struct FitShared {
   float g[kFitMaxTaps * 3];
   LayerExtent ext[DISK_MAX_LAYERS];
   float red[kFitMaxWarps];
+  float closs;  // this CTA's share of the loss
+  // per-(chunk, tap) partial tap gradients of the warps of this CTA
+  float part[3 * (kFitMaxWarps * kFitMaxCluster > DISK_MAX_TAPS ? kFitMaxWarps * kFitMaxCluster
+                                                                   : DISK_MAX_TAPS)];
 };
+
+namespace cg = cooperative_groups;
+
+// Barrier over the CTAs that share a target (release / acquire at cluster
+// scope, global writes fenced first); a plain block barrier when CL == 1.
+template <int CL>
+__device__ __forceinline__ void target_sync() {
+  if (CL == 1) {
+    __syncthreads();
+  } else {
+    __threadfence();
+    cg::this_cluster().sync();
+  }
+}
+
+template <int CL>
+__device__ __forceinline__ unsigned target_rank() {
+  if (CL == 1) return 0;
+  return cg::this_cluster().block_rank();
+}
+
+// Address of *p in the shared memory of CTA r of the cluster.
+template <int CL>
+__device__ __forceinline__ const float *rank_ptr(const float *p, unsigned r) {
+  if (CL == 1) return p;
+  return cg::this_cluster().map_shared_rank(const_cast<float *>(p), r);
+}
 
 // taps (pixels) from normalised parameters; layer extents from the taps.
 __device__ void make_taps(FitShared &sh, int L, int T, float s) {
@@ -256,29 +295,34 @@ __device__ void make_taps(FitShared &sh, int L, int T, float s) {
 }
 
 // Forward cascade on planes act[0..L]; returns the loss and leaves dL/dI_L in
-// gL (box of half-width max(S_L, h)).
+// gL (box of half-width max(S_L, h)).  Sweeps are split over the CL CTAs.
+template <int CL>
 __device__ float forward_loss(FitShared &sh, const FitArgs &A, const FitMeta &m, float *const *act,
-                              float *gL, const float *tgt) {
+                              float *gL, const float *tgt, unsigned rank) {
   const int L = A.L, T = A.T, R = m.R, N = 2 * R + 1, K = m.K, h = (K - 1) / 2;
-  // impulse: zero the footprint layer 1 reads, then the unit impulse at c
-  zero_frame(act[0], R, -1, 2 * sh.ext[0].H);
-  __syncthreads();
-  if (threadIdx.x == 0) act[0][R * N + R] = 1.f;
-  __syncthreads();
+  const int tid = (int)rank * blockDim.x + threadIdx.x, nthr = blockDim.x * CL;
+  {
+    // the footprint layer 1 reads: zeros, with the unit impulse at c
+    const int b0 = min(2 * sh.ext[0].H, R), side0 = 2 * b0 + 1;
+    for (int j = tid; j < side0 * side0; j += nthr) {
+      const int v = j / side0 - b0, u = j % side0 - b0;
+      act[0][(R + v) * N + (R + u)] = (u == 0 && v == 0) ? 1.f : 0.f;
+    }
+  }
+  target_sync<CL>();
   for (int l = 0; l < L; ++l) {
     const int S = sh.ext[l].S;
-    canvas_layer(act[l], act[l + 1], R, S, sh.taps + l * T, T, sh.ext[l].H, 1.f);
-    __syncthreads();
+    canvas_layer(act[l], act[l + 1], R, S, sh.taps + l * T, T, sh.ext[l].H, 1.f, tid, nthr);
     const int reach = (l + 1 < L) ? S + 2 * sh.ext[l + 1].H : max(S, h);
-    zero_frame(act[l + 1], R, S, reach);
-    __syncthreads();
+    zero_frame(act[l + 1], R, S, reach, tid, nthr);  // disjoint from the layer's box
+    target_sync<CL>();
   }
   const int bx = max(sh.ext[L - 1].S, h);
   const float inv = 1.f / ((float)K * (float)K);
   const float *KL = act[L];
   float part = 0.f;
   const int side = 2 * bx + 1;
-  for (int j = threadIdx.x; j < side * side; j += blockDim.x) {
+  for (int j = tid; j < side * side; j += nthr) {
     const int v = j / side - bx, u = j % side - bx;
     const float t = (abs(v) <= h && abs(u) <= h) ? tgt[(v + h) * K + (u + h)] : 0.f;
     const float d = KL[(R + v) * N + (R + u)] - t;
@@ -293,59 +337,83 @@ __device__ float forward_loss(FitShared &sh, const FitArgs &A, const FitMeta &m,
     }
     gL[(R + v) * N + (R + u)] = g;
   }
-  return block_sum(part, sh.red);
+  part = block_sum(part, sh.red);
+  if (threadIdx.x == 0) sh.closs = part;
+  target_sync<CL>();
+  float loss = 0.f;
+  for (unsigned r = 0; r < (unsigned)CL; ++r) loss += *rank_ptr<CL>(&sh.closs, r);
+  return loss;
 }
 
 // Tap gradients of every layer into sh.g (pixel units); ga/gb are the two
 // adjoint planes (ga holds dL/dI_L on entry).
+template <int CL>
 __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, float *const *act,
-                         float *ga, float *gb) {
+                         float *ga, float *gb, unsigned rank) {
   const int L = A.L, T = A.T, R = m.R, N = 2 * R + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nwt = nw * CL, gwarp = (int)rank * nw + warp;
+  const int tid = (int)rank * blockDim.x + threadIdx.x, nthr = blockDim.x * CL;
   float *G = ga, *Gn = gb;
   for (int l = L - 1; l >= 0; --l) {
-    const int S = sh.ext[l].S, side = 2 * S + 1, halo = sh.ext[l].H;
+    const int S = sh.ext[l].S, halo = sh.ext[l].H;
     const float *prev = act[l];
-    // dL/dw, dL/do of every tap of layer l: one warp per tap, lanes over pixels
-    for (int i = warp; i < T; i += nw) {
+    // dL/dw, dL/do of every tap of layer l: `chunks` warps of the cluster
+    // per tap (every warp works when T is below the warp count), each over
+    // every chunks-th row of the support box, lanes over its pixels.  Unit
+    // wi = c * T + i is done by global warp wi mod nwt, which keeps its sums
+    // in its own CTA's part[] slot wi; they are added in chunk order below.
+    const int chunks = max(1, nwt / T);
+    for (int wi = gwarp; wi < T * chunks; wi += nwt) {
+      const int i = wi % T, c = wi / T;
       const float4 t = sh.taps[l * T + i];
       float fx, fy;
       const int nx = min(max(split_floor(t.x, fx), -halo), halo - 1);
       const int ny = min(max(split_floor(t.y, fy), -halo), halo - 1);
       float gw = 0.f, gdx = 0.f, gdy = 0.f;
-      for (int v = -S; v <= S; ++v) {
+      for (int v = -S + c; v <= S; v += chunks) {
         const float *grow = G + (R + v) * N + R;
         const float *prow = prev + (R + v + ny) * N + R + nx;
         for (int u = -S + lane; u <= S; u += 32) {
           const float g = grow[u];
           const float *q = prow + u;
-          const float a = q[0], bq = q[1], c = q[N], d = q[N + 1];
-          const float top = a + fx * (bq - a), bot = c + fx * (d - c);
+          const float a = q[0], bq = q[1], cq = q[N], d = q[N + 1];
+          const float top = a + fx * (bq - a), bot = cq + fx * (d - cq);
           gw += g * (top + fy * (bot - top));
-          gdx += g * ((1.f - fy) * (bq - a) + fy * (d - c));
+          gdx += g * ((1.f - fy) * (bq - a) + fy * (d - cq));
           gdy += g * (bot - top);
         }
       }
       gw = warp_sum(gw); gdx = warp_sum(gdx); gdy = warp_sum(gdy);
       if (lane == 0) {
-        float *gg = sh.g + ((size_t)l * T + i) * 3;
-        gg[0] = gdx * t.z; gg[1] = gdy * t.z; gg[2] = gw;
+        float *pp = sh.part + (size_t)wi * 3;
+        pp[0] = gdx * t.z; pp[1] = gdy * t.z; pp[2] = gw;
       }
     }
-    (void)side;
+    target_sync<CL>();
+    for (int j = threadIdx.x; j < T * 3; j += blockDim.x) {
+      const int i = j / 3, k = j % 3;
+      float acc = 0.f;
+      for (int c = 0; c < chunks; ++c) {
+        const int wi = c * T + i;
+        acc += rank_ptr<CL>(sh.part, (unsigned)((wi % nwt) / nw))[(size_t)wi * 3 + k];
+      }
+      sh.g[(size_t)l * T * 3 + j] = acc;
+    }
     if (l > 0) {
       // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
-      canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.taps + l * T, T, halo, -1.f);
+      canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.taps + l * T, T, halo, -1.f, tid, nthr);
     }
-    __syncthreads();
+    target_sync<CL>();  // the adjoint plane is whole; every CTA has read the partial sums
     float *t = G; G = Gn; Gn = t;
   }
 }
 
-template <int NT>
+template <int NT, int CL>
 __global__ void __launch_bounds__(NT) fit_kernel(FitArgs A) {
   __shared__ FitShared sh;
-  const int b = A.order[blockIdx.x];
+  const unsigned rank = target_rank<CL>();
+  const int b = A.order[blockIdx.x / CL];
   const FitMeta m = A.meta[b];
   const int L = A.L, T = A.T, P = L * T * 3, N = 2 * m.R + 1;
   const size_t plane = (size_t)N * N;
@@ -367,16 +435,18 @@ __global__ void __launch_bounds__(NT) fit_kernel(FitArgs A) {
   float b1t = 1.f, b2t = 1.f;
   for (int step = 0; step < A.steps || (A.mode == 1 && step == 0); ++step) {
     make_taps(sh, L, T, s);
-    const float loss = forward_loss(sh, A, m, act, ga, tgt);
-    __syncthreads();
-    backward(sh, A, m, act, ga, gb);
-    __syncthreads();
+    const float loss = forward_loss<CL>(sh, A, m, act, ga, tgt, rank);
+    backward<CL>(sh, A, m, act, ga, gb, rank);
     if (A.mode == 1) {
-      for (int j = threadIdx.x; j < P; j += blockDim.x) A.grad_out[(size_t)b * P + j] = sh.g[j];
-      if (threadIdx.x == 0 && A.loss_out) A.loss_out[b] = loss;
+      if (rank == 0) {
+        for (int j = threadIdx.x; j < P; j += blockDim.x) A.grad_out[(size_t)b * P + j] = sh.g[j];
+        if (threadIdx.x == 0 && A.loss_out) A.loss_out[b] = loss;
+      }
+      target_sync<CL>();  // no CTA leaves while another may read its shared memory
       return;
     }
-    if (threadIdx.x == 0 && A.loss_hist) A.loss_hist[(size_t)b * (A.steps + 1) + step] = loss;
+    if (rank == 0 && threadIdx.x == 0 && A.loss_hist)
+      A.loss_hist[(size_t)b * (A.steps + 1) + step] = loss;
     const float lr = A.steps > 1 ? A.lr0 + (A.lr1 - A.lr0) * (float)step / (float)(A.steps - 1) : A.lr0;
     b1t *= b1;
     b2t *= b2;
@@ -395,13 +465,16 @@ __global__ void __launch_bounds__(NT) fit_kernel(FitArgs A) {
   }
   // final loss at the fitted parameters
   make_taps(sh, L, T, s);
-  const float loss = forward_loss(sh, A, m, act, ga, tgt);
-  if (threadIdx.x == 0) {
-    if (A.loss_out) A.loss_out[b] = loss;
-    if (A.loss_hist) A.loss_hist[(size_t)b * (A.steps + 1) + A.steps] = loss;
+  const float loss = forward_loss<CL>(sh, A, m, act, ga, tgt, rank);
+  if (rank == 0) {
+    if (threadIdx.x == 0) {
+      if (A.loss_out) A.loss_out[b] = loss;
+      if (A.loss_hist) A.loss_hist[(size_t)b * (A.steps + 1) + A.steps] = loss;
+    }
+    for (int j = threadIdx.x; j < P; j += blockDim.x)
+      th[j] = (j % 3 == 2) ? sh.q[j] : sh.q[j] * s;
   }
-  for (int j = threadIdx.x; j < P; j += blockDim.x)
-    th[j] = (j % 3 == 2) ? sh.q[j] : sh.q[j] * s;
+  target_sync<CL>();  // no CTA leaves while another may read its shared memory
 }
 
 // ---- host side -----------------------------------------------------------------
@@ -461,23 +534,62 @@ int plan_fit(const int *sizes, int batch, int L, FitPlan &plan) {
 }
 
 // ---- launch-configuration autotuner ----------------------------------------------
-// The fit CTA size (256, 512 or 1024 threads per target) trades the
-// parallelism of one target's canvas sweeps against how many targets share an
-// SM.  disk_fit_autotune times each on the caller's batch and records the
-// fastest per (L, T, largest target size in 32-pixel buckets).
+// The launch configuration -- threads per CTA (256, 512, 1024) and CTAs per
+// target (1, 2 or 4, a thread-block cluster) -- trades the parallelism of one
+// target's canvas sweeps against how many targets share the GPU; the largest
+// target of a batch sets the makespan when it runs on one SM.
+// disk_fit_autotune times each on the caller's batch and records the fastest
+// per (L, T, largest target size in 32-pixel buckets).
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_tune;
 
-int tuned_threads(int L, int T, int kmax) {
+// A launch configuration is encoded as threads * 16 + CTAs per target.
+int tuned_config(int L, int T, int kmax) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune.find(std::make_tuple(L, T, (kmax + 31) / 32));
-  return it == g_tune.end() ? 512 : it->second;
+  return it == g_tune.end() ? 512 * 16 + 1 : it->second;
 }
+
+template <int NT, int CL>
+cudaError_t launch_fit(const FitArgs &A, cudaStream_t s) {
+  if (CL == 1) {
+    fit_kernel<NT, 1><<<A.batch, NT, 0, s>>>(A);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(A.batch * CL);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fit_kernel<NT, CL>, A);
+}
+
+cudaError_t launch_fit_config(int config, const FitArgs &A, cudaStream_t s) {
+  switch (config) {
+    case 256 * 16 + 1: return launch_fit<256, 1>(A, s);
+    case 1024 * 16 + 1: return launch_fit<1024, 1>(A, s);
+    case 512 * 16 + 2: return launch_fit<512, 2>(A, s);
+    case 1024 * 16 + 2: return launch_fit<1024, 2>(A, s);
+    case 512 * 16 + 4: return launch_fit<512, 4>(A, s);
+    case 1024 * 16 + 4: return launch_fit<1024, 4>(A, s);
+    default: return launch_fit<512, 1>(A, s);
+  }
+}
+
+constexpr int kFitConfigs[] = {256 * 16 + 1, 512 * 16 + 1, 1024 * 16 + 1, 512 * 16 + 2,
+                               1024 * 16 + 2, 512 * 16 + 4, 1024 * 16 + 4};
 
 int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, int steps,
             float lr0, float lr1, int init, int loss, float eps, unsigned long long seed,
             float *d_theta, float *d_loss, float *d_hist, float *d_grad, int mode,
-            cudaStream_t s, int threads = 0) {
+            cudaStream_t s, int config = 0) {
   if (!d_targets || !sizes || !d_theta) return fail(DISK_ERR_INVALID_ARG, "null pointer");
   if (batch < 1 || L < 1 || L > DISK_MAX_LAYERS || T < 1 || T > DISK_MAX_TAPS)
     return fail(DISK_ERR_INVALID_ARG, "batch >= 1, L in [1, 16], T in [1, 64] required");
@@ -530,11 +642,7 @@ int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, i
   if (mode == 0 && init != 0) fit_init_kernel<<<batch, kFitThreads, 0, s>>>(A, init, seed);
   e = cudaGetLastError();
   if (e == cudaSuccess) {
-    const int nt = threads > 0 ? threads : tuned_threads(L, T, plan.kmax);
-    if (nt == 256) fit_kernel<256><<<batch, 256, 0, s>>>(A);
-    else if (nt == 1024) fit_kernel<1024><<<batch, 1024, 0, s>>>(A);
-    else fit_kernel<512><<<batch, 512, 0, s>>>(A);
-    e = cudaGetLastError();
+    e = launch_fit_config(config > 0 ? config : tuned_config(L, T, plan.kmax), A, s);
   }
   cudaFreeAsync(buf, s);
   if (e != cudaSuccess) return cuda_fail(e, "launch fit kernels");
@@ -565,7 +673,7 @@ extern "C" int disk_fit_loss_grad(const float *d_targets, const int *sizes, int 
 }
 
 extern "C" int disk_fit_autotune(const float *d_targets, const int *sizes, int batch, int L, int T,
-                                 int loss, float eps, int *chosen_threads, void *stream) {
+                                 int loss, float eps, int *chosen_config, void *stream) {
   if (!sizes || batch < 1) return fail(DISK_ERR_INVALID_ARG, "bad batch");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float *theta = nullptr;
@@ -574,26 +682,25 @@ extern "C" int disk_fit_autotune(const float *d_targets, const int *sizes, int b
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int cand[3] = {256, 512, 1024};
   float best_ms = 1e30f;
-  int best = 512, rc = DISK_OK;
+  int best = 512 * 16 + 1, rc = DISK_OK;
   int kmax = 0;
   for (int b = 0; b < batch; ++b) kmax = std::max(kmax, sizes[b]);
-  for (int c = 0; c < 3 && rc == DISK_OK; ++c) {
+  for (int c = 0; c < (int)(sizeof(kFitConfigs) / sizeof(int)) && rc == DISK_OK; ++c) {
     // same start for every candidate: the radial initialisation, then 4 steps
     rc = run_fit(d_targets, sizes, batch, L, T, 0, 1e-3f, 1e-4f, 1, loss, eps, 0, theta, nullptr,
-                 nullptr, nullptr, 0, s, cand[c]);
+                 nullptr, nullptr, 0, s, kFitConfigs[c]);
     if (rc) break;
     cudaEventRecord(e0, s);
     rc = run_fit(d_targets, sizes, batch, L, T, 4, 1e-3f, 1e-4f, 0, loss, eps, 0, theta, nullptr,
-                 nullptr, nullptr, 0, s, cand[c]);
+                 nullptr, nullptr, 0, s, kFitConfigs[c]);
     cudaEventRecord(e1, s);
     if (rc) break;
     cudaError_t e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = cand[c]; }
+    if (ms < best_ms) { best_ms = ms; best = kFitConfigs[c]; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -603,6 +710,16 @@ extern "C" int disk_fit_autotune(const float *d_targets, const int *sizes, int b
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[std::make_tuple(L, T, (kmax + 31) / 32)] = best;
   }
-  if (chosen_threads) *chosen_threads = best;
+  if (chosen_config) *chosen_config = best;
+  return DISK_OK;
+}
+
+extern "C" int disk_fit_set_config(int L, int T, int kmax, int config) {
+  bool known = false;
+  for (int c : kFitConfigs) known = known || c == config;
+  if (!known) return fail(DISK_ERR_INVALID_ARG, "unknown fit launch configuration");
+  if (L < 1 || T < 1 || kmax < 1) return fail(DISK_ERR_INVALID_ARG, "bad L, T or kmax");
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[std::make_tuple(L, T, (kmax + 31) / 32)] = config;
   return DISK_OK;
 }

@@ -78,6 +78,7 @@ def lib() -> ctypes.CDLL:
             "disk_fit": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, ctypes.c_float, _i, _i,
                               ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
             "disk_fit_autotune": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _ip, _vp]),
+            "disk_fit_set_config": (_i, [_i, _i, _i, _i]),
             "disk_mlp_param_count": (ctypes.c_longlong, [_i, _i, _i, _i]),
             "disk_mlp_init": (_i, [_vp, _i, _i, _i, _i, ctypes.c_uint64, _vp]),
             "disk_mlp_forward": (_i, [_vp, _i, _i, _i, _i, _vp, _i, _vp, _vp]),
@@ -434,13 +435,20 @@ def fit(packed, sizes, L: int, T: int, steps: int, lr0: float = 1e-3, lr1: float
 
 
 def fit_autotune(packed, sizes, L: int, T: int, loss: int = LOSS_MSE, eps: float = 0.0,
-                 stream=None) -> int:
-    """Pick the fit kernel's CTA size for this batch shape; returns it."""
+                 stream=None) -> tuple:
+    """Pick the fit kernel's launch configuration for this batch shape;
+    returns (threads per CTA, CTAs per target)."""
     out = ctypes.c_int()
     _check("disk_fit_autotune", lib().disk_fit_autotune(
         _vp(packed.data_ptr()), _int_arr(sizes), len(sizes), L, T, loss, eps,
         ctypes.byref(out), _stream(stream)))
-    return out.value
+    return out.value // 16, out.value % 16
+
+
+def fit_set_config(L: int, T: int, kmax: int, threads: int, ctas: int):
+    """Record the fit launch configuration (threads per CTA, CTAs per target)
+    for batches with this L, T and largest target size."""
+    _check("disk_fit_set_config", lib().disk_fit_set_config(L, T, kmax, threads * 16 + ctas))
 
 
 def fit_loss_grad(packed, sizes, theta, loss: int = LOSS_MSE, eps: float = 0.0, stream=None):
