@@ -298,6 +298,8 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
     mse = float(((o - dd) ** 2).mean().item())
     out["fit"] = fit_leg(stream)
     out["gaussian_tilt_shift"] = gaussian_leg(d_img, flush, stream)
+    out["bokeh_1080p_fp32"] = bokeh1080_leg(flush, stream)
+    out["small_256_fp32"] = small256_leg(stream)
     out["radial_motion"] = rotated_leg(wl.RM, "line12_L3T8.dkb", False, d_img, flush, stream)
     out["rotational_bokeh"] = rotated_leg(wl.RB, "cateye12_L4T16.dkb", True, d_img, flush, stream)
     out["dense_sv"] = {"value": px / (dms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": dms,
@@ -319,6 +321,79 @@ def _timed(fn, flush, stream, n):
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b))
     return float(np.median(ts))
+
+
+def bokeh1080_leg(flush, stream):
+    """1920 x 1080 RGB FP32 depth-of-field: 16 fitted disks (radius 1..32
+    px, L=4, T=16) under a smooth circle-of-confusion map, against the dense
+    spatially varying disk convolution (65 x 65 node kernels)."""
+    import torch
+
+    from paper_2512_04556_gb300 import disk
+    c = wl.C2
+    H, W = c["H"], c["W"]
+    img = torch.from_numpy(wl.image_rects(H, W, 3)).cuda()
+    maps = torch.from_numpy(wl.param_map(H, W, *c["map_range"], sigma=c["map_sigma"])[None]).cuda()
+    b = disk.Basis.load(os.path.join(BASES, "disk16_L4T16.dkb"))
+    tiles = disk.sv_filter_autotune(b, img, maps, stream=stream)
+    out = torch.empty_like(img)
+    ms = _timed(lambda: disk.sv_filter(b, img, maps, out=out, stream=stream), flush, stream, 10)
+    nodes = np.linspace(1.0, 32.0, 16)
+    lut = torch.from_numpy(wl.disk_lut(nodes, c["dense_K"])).cuda()
+    dense = torch.empty_like(img)
+    dms = _timed(lambda: disk.dense_sv([nodes], lut, img, maps, out=dense, stream=stream),
+                 flush, stream, 3)
+    mse = float(((out - dense) ** 2).mean().item())
+    px = H * W
+    return {"value": px / (ms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": ms,
+            "L": b.L, "T": b.T, "tile": ", ".join(f"32x{8 * p}" for p in tiles),
+            "dense_ms": dms, "dense_kernel": f"{c['dense_K']}x{c['dense_K']}, 16 disks",
+            "speedup_disk_vs_dense": dms / ms,
+            "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20)))}
+
+
+def small256_leg(stream, n=200):
+    """256 x 256 RGB FP32 with a random 4-node basis (L=3, T=8): a frame this
+    small is bound by launch latency; timed as n back-to-back calls and as
+    the same calls replayed from a CUDA graph (inputs stay in L2)."""
+    import torch
+
+    from paper_2512_04556_gb300 import disk
+    img_np, maps_np, _, nodes, theta = wl.c1_inputs()
+    img, maps = torch.from_numpy(img_np).cuda(), torch.from_numpy(maps_np).cuda()
+    b = disk.Basis.from_arrays([nodes], theta)
+    out = torch.empty_like(img)
+    for _ in range(5):
+        disk.sv_filter(b, img, maps, out=out, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        disk.sv_filter(b, img, maps, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    eager_us = e0.elapsed_time(e1) / n * 1e3
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        disk.sv_filter(b, img, maps, out=out)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=side):
+            for _ in range(20):
+                disk.sv_filter(b, img, maps, out=out)
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(n // 20):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    graph_us = e0.elapsed_time(e1) / n * 1e3
+    px = 256 * 256
+    return {"value": px / (graph_us * 1e-6) / 1e9, "unit": "Gpix/s", "us_per_frame_graph": graph_us,
+            "us_per_frame_eager": eager_us, "launches_per_frame": b.L, "l2": "resident (0.8 MB)"}
 
 
 def gaussian_leg(d_img, flush, stream):
@@ -551,6 +626,7 @@ def main():
         line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"],
                     clocks=res["clocks"], gpu_launches=res["gpu_launches"])
         for k in ("roofline", "e2e", "dense_sv", "backward_image", "fit", "gaussian_tilt_shift",
+                  "bokeh_1080p_fp32", "small_256_fp32",
                   "radial_motion", "rotational_bokeh", "smem_model"):
             if k in res:
                 line[k] = res[k]
