@@ -274,6 +274,21 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
     bms = float(np.median(bts))
     out["backward_image"] = {"value": px / (bms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": bms,
                              "grad_in": "fp32", "grad_out": "fp16"}
+    # full backward: image and basis gradients (layer inputs recomputed)
+    disk.sv_filter_backward(basis, d_img, g_out, d_maps, stream=stream)
+    torch.cuda.synchronize()
+    fts = []
+    for _ in range(3):
+        flush.fill_(2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        disk.sv_filter_backward(basis, d_img, g_out, d_maps, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fts.append(a.elapsed_time(b))
+    fms = float(np.median(fts))
+    out["backward_full"] = {"value": px / (fms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": fms,
+                            "outputs": "grad image (fp32) and grad basis [64][4][24][3]"}
 
     # dense spatially varying convolution on the same frame (Eq. 1 per pixel)
     n0 = np.linspace(2.0, 40.0, 16)
@@ -625,7 +640,8 @@ def main():
     if rank == 0:
         line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"],
                     clocks=res["clocks"], gpu_launches=res["gpu_launches"])
-        for k in ("roofline", "e2e", "dense_sv", "backward_image", "fit", "gaussian_tilt_shift",
+        for k in ("roofline", "e2e", "dense_sv", "backward_image", "backward_full", "fit",
+                  "gaussian_tilt_shift",
                   "bokeh_1080p_fp32", "small_256_fp32",
                   "radial_motion", "rotational_bokeh", "smem_model"):
             if k in res:

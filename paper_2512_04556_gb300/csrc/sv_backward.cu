@@ -172,6 +172,35 @@ __device__ __forceinline__ float tg_warp_sum(float v) {
   return v;
 }
 
+// Warp sums of N = 16 (or 8) values per lane by recursive halving: at each
+// step a lane keeps half of its values and adds its partner's copies of that
+// half, so the whole reduction takes N - 1 + (5 - log2 N) shuffles instead of
+// 5 N.  On return lane l holds in v[0] the warp sum of value
+// tg_scatter_index<N>(l) (lanes l and l ^ 1 hold the same one for N = 16).
+template <int N>
+__device__ __forceinline__ int tg_scatter_index(int lane) {
+  return N == 16 ? (((lane >> 4) & 1) << 3) | (((lane >> 3) & 1) << 2) | (((lane >> 2) & 1) << 1) |
+                       ((lane >> 1) & 1)
+                 : (((lane >> 4) & 1) << 2) | (((lane >> 3) & 1) << 1) | ((lane >> 2) & 1);
+}
+
+template <int N>
+__device__ __forceinline__ void tg_warp_reduce_scatter(float (&v)[N], int lane) {
+#pragma unroll
+  for (int n = N / 2, o = 16; n >= 1; n /= 2, o /= 2) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      const float keep = upper ? v[k + n] : v[k];
+      const float give = upper ? v[k] : v[k + n];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+    }
+  }
+  // the offsets not used for halving sum the one remaining value
+#pragma unroll
+  for (int o = N == 16 ? 1 : 2; o >= 1; o /= 2) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+}
+
 __device__ __forceinline__ float4 tg_staged(const float4 &v) { return v; }
 __device__ __forceinline__ float4 tg_staged(const uint2 &v) { return unpack_half4(v); }
 
@@ -278,14 +307,18 @@ sv_theta_grad_kernel(const __grid_constant__ TgParams P) {
         }
       }
 #pragma unroll
-      for (int k = 0; k < (DIMS == 2 ? 12 : 6); ++k) v[k] = tg_warp_sum(v[k]);
-      if (lane == 0) {
-        const int nodes[4] = {n00, n10, n01, n11};
+      // reduce the 12 (2-D) or 6 (1-D) node-gradient values over the warp
+      // in one reduce-scatter; one lane per value then adds it
+      constexpr int NV = DIMS == 2 ? 16 : 8;
+      float r[NV];
 #pragma unroll
-        for (int k = 0; k < (DIMS == 2 ? 4 : 2); ++k) {
-          float *dst = gacc + (nodes[k] * T + i) * 3;
-          atomicAdd(dst, v[3 * k]); atomicAdd(dst + 1, v[3 * k + 1]); atomicAdd(dst + 2, v[3 * k + 2]);
-        }
+      for (int k = 0; k < NV; ++k) r[k] = k < (DIMS == 2 ? 12 : 6) ? v[k] : 0.f;
+      tg_warp_reduce_scatter<NV>(r, lane);
+      const int idx = tg_scatter_index<NV>(lane);
+      const bool owner = NV == 16 ? (lane & 1) == 0 : (lane & 3) == 0;
+      if (owner && idx < (DIMS == 2 ? 12 : 6)) {
+        const int node = (idx / 3) == 0 ? n00 : (idx / 3) == 1 ? n10 : (idx / 3) == 2 ? n01 : n11;
+        atomicAdd(gacc + (node * T + i) * 3 + idx % 3, r[0]);
       }
     }
   } else {
