@@ -1,18 +1,23 @@
 // One layer of the spatially varying cascade (Sec. 4.3 Eq. 9 + Sec. 3.2
 // Eq. 3): the kernel template shared by the 1-D and 2-D translation units.
 //
-// Each CTA owns a 32 x 32 output tile.  It stages the layer's source region
-// (tile + the layer's halo, clamp-to-edge) into shared memory as FP32 planes
-// -- (r, g) pairs in one, b (or (b, a) pairs) in another -- converting FP16
-// sources once per staged pixel instead of once per tap and corner; a warp's
-// 32 lanes (consecutive columns) read consecutive entries.  FP16 images keep
-// FP16 planes in HBM; arithmetic and accumulation are FP32.
-// Every thread owns PIX pixels of one column (rows r, r+8, ...).
+// Each CTA owns a 32 x 16 or 32 x 32 output tile (PIX = 2 or 4 pixels of one
+// column per thread, rows r, r + 8, ...).  It stages the layer's source
+// region (tile + the layer's halo, clamp-to-edge) into shared memory as FP32
+// planes -- (r, g) pairs in one, b (or (b, a) pairs) in another -- converting
+// FP16 sources once per staged pixel instead of once per tap and corner; a
+// warp's 32 lanes (consecutive columns) read consecutive entries.  A planar
+// FP32 intermediate is copied in by the tensor-memory accelerator; the
+// caller's image goes through registers.  The layer's node taps are copied
+// into shared memory beside the region.  Arithmetic and accumulation are FP32.
 // When each thread's pixels sit in one kernel-space cell -- the common case,
 // parameter maps being smooth -- the node taps of each tap index are fetched
-// once per thread (constant-bank loads) and blended for its pixels with each
-// pixel's own weights; warps with a thread whose pixels straddle cells take
-// the per-pixel path.
+// once per thread (128-bit shared-memory broadcasts) and blended for its
+// pixels with each pixel's own weights; warps with a thread whose pixels
+// straddle cells take the per-pixel path.
+// The rotated variant (ROT) turns every pixel's blended tap offsets by that
+// pixel's angle before sampling: the runtime form of the rotational and
+// radial blur effects of Sec. 5.3, exact for the complex's impulse response.
 #pragma once
 
 #include <cuda.h>
