@@ -253,6 +253,14 @@ int disk_sv_filter_frames(const disk_basis *basis, const void *const *h_in,
  * call (outputs written since then are then incomplete). */
 int disk_device_status(void *stream);
 
+/* Self-test of the bounded waits (failure detection without a GPU fault):
+ * launches one block that arms a tile-copy barrier no copy will complete and
+ * waits at most `iterations` polls (1 .. 2^24), then records
+ * DISK_ERR_TIMEOUT in the device status word exactly as a layer kernel whose
+ * copy did not land would; a following disk_device_status reports it.
+ * Asynchronous on `stream`. */
+int disk_selftest_bounded_wait(long long iterations, void *stream);
+
 /* Records one tile configuration (pixels per thread: 2 or 4) for every
  * layer, for this (H, W, C, dtype), in the basis handle. */
 int disk_sv_filter_set_tile(const disk_basis *basis, int H, int W, int C, int dtype,

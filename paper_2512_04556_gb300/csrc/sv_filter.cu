@@ -46,6 +46,24 @@ int launch_layer(int dims, bool shared_taps, bool rot, int src, int dst, int C,
                      : launch_sv_layer<2, kSvTapsGlobal, false>(src, dst, C, P, s, pix);
 }
 
+// Exercises the bounded wait of the tile copies: the block arms an
+// mbarrier for 16 bytes that no copy will deliver, waits at most `iters`
+// polls, and records DISK_ERR_TIMEOUT like a layer kernel whose copy did not
+// land.  Nothing faults or hangs: the wait ends by its limit.
+__global__ void wait_selftest_kernel(int *err, long long iters) {
+  __shared__ __align__(8) unsigned long long bar;
+  const unsigned b = smem_addr(&bar);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(16u)
+                 : "memory");
+  }
+  __syncthreads();
+  const bool landed = mbar_wait(b, 0, iters);
+  if (!__syncthreads_and(landed) && threadIdx.x == 0) atomicExch(err, DISK_ERR_TIMEOUT);
+}
+
 namespace {
 
 // Staging geometry of layer l: halo rows above and below the tile, halo_x
@@ -411,5 +429,15 @@ extern "C" int disk_sv_filter_set_tile(const disk_basis *b, int H, int W, int C,
       return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory for this tile");
   std::lock_guard<std::mutex> lock(b->tune_mu);
   b->tune_pix[tune_key(H, W, C, dtype, false)] = std::vector<int>(b->L, pix);
+  return DISK_OK;
+}
+
+extern "C" int disk_selftest_bounded_wait(long long iterations, void *stream) {
+  if (iterations < 1 || iterations > (1ll << 24))
+    return fail(DISK_ERR_INVALID_ARG, "iterations must be in [1, 2^24]");
+  int *err = device_error_word();
+  if (!err) return fail(DISK_ERR_CUDA, "device status word unavailable");
+  wait_selftest_kernel<<<1, 64, 0, static_cast<cudaStream_t>(stream)>>>(err, iterations);
+  DISK_TRY_CUDA(cudaGetLastError(), "launch wait_selftest_kernel");
   return DISK_OK;
 }

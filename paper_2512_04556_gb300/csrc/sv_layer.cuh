@@ -99,8 +99,9 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
 }
 
 // Bounded wait for phase `parity` of mbarrier bar; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (long long i = 0; i < kSvMaxWaitIters; ++i) {
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
+                                          long long max_iters = kSvMaxWaitIters) {
+  for (long long i = 0; i < max_iters; ++i) {
     unsigned ok;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"

@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
             "disk_sv_filter_autotune": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _ip, _vp]),
             "disk_sv_filter_set_tile": (_i, [_vp, _i, _i, _i, _i, _i]),
             "disk_device_status": (_i, [_vp]),
+            "disk_selftest_bounded_wait": (_i, [ctypes.c_longlong, _vp]),
             "disk_sv_filter_frames": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                            ctypes.POINTER(_vp), _i, _i, _i, _i, _i, _vp]),
             "disk_sv_filter_rotated": (_i, [_vp, _vp, _sz, _vp, _sz, _i, _i, _i, _i, _vp, _vp, _vp]),
@@ -299,6 +300,11 @@ def device_status(stream=None):
     """Raises DiskError (DISK_ERR_TIMEOUT) if a kernel gave up a bounded wait
     since the last call; synchronises the stream."""
     _check("disk_device_status", lib().disk_device_status(_stream(stream)))
+
+
+def selftest_bounded_wait(iterations: int = 1000, stream=None):
+    """Queue a block whose bounded wait runs out (see device_status)."""
+    _check("disk_selftest_bounded_wait", lib().disk_selftest_bounded_wait(iterations, _stream(stream)))
 
 
 def sv_filter_set_tile(basis: Basis, H: int, W: int, C: int, dtype: int, pix: int):

@@ -149,3 +149,19 @@ def test_device_status_clean_after_filtering(torch_cuda):
     img, maps, axes, th, angle = _case(64, 96, 2, 3, 6, 2.0, 23)
     _gpu(torch_cuda, img, maps, axes, th, angle)
     disk.device_status()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(torch_cuda):
+    """A tile-copy wait that runs out (a barrier nothing completes) records
+    DISK_ERR_TIMEOUT, the status clears once read, and the context keeps
+    working: the filter still matches the oracle afterwards."""
+    from paper_2512_04556_gb300 import disk
+    disk.device_status()
+    disk.selftest_bounded_wait(2000)
+    with pytest.raises(disk.DiskError) as e:
+        disk.device_status()
+    assert e.value.code == -6
+    disk.device_status()
+    img, maps, axes, th, angle = _case(40, 50, 2, 3, 6, 2.0, 29)
+    got = _gpu(torch_cuda, img, maps, axes, th, angle)
+    assert rel_err(got, _oracle(img, maps, axes, th, angle)) <= TOL32
