@@ -1,8 +1,9 @@
 // One layer of the spatially varying cascade (Sec. 4.3 Eq. 9 + Sec. 3.2
 // Eq. 3): the kernel template shared by the 1-D and 2-D translation units.
 //
-// Each CTA owns a 32 x 16 or 32 x 32 output tile (PIX = 2 or 4 pixels of one
-// column per thread, rows r, r + 8, ...).  It stages the layer's source
+// Each CTA owns a 32 x 16 or 32 x 32 output tile (PIX = 2 or 4 vertically
+// adjacent pixels of one column per thread; a pair of them shares the
+// corner row between them when their integer offsets agree).  It stages the layer's source
 // region (tile + the layer's halo, clamp-to-edge) into shared memory as FP32
 // planes -- (r, g) pairs in one, b (or (b, a) pairs) in another -- converting
 // FP16 sources once per staged pixel instead of once per tap and corner; a
@@ -207,6 +208,87 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   add_corner<CH>(st, e + RW + 1, w11, acc);
 }
 
+// Two vertically adjacent pixels of one thread and one tap.  Their sample
+// points usually have the same integer offset (the offsets vary slowly
+// across pixels), and then the lower pixel's top corners are the upper
+// pixel's bottom corners: they are read from shared memory once.
+template <int DIMS, int CH, bool ROT>
+__device__ __forceinline__ void sv_tap_pair(const float4 &q00, const float4 &q10, const float4 &q01,
+                                            const float4 &q11, const CellPairs &a0,
+                                            const CellPairs &a1, const RotPairs &rot0,
+                                            const RotPairs &rot1, const Staged &st, int base0, int RW,
+                                            Acc &acc0, Acc &acc1) {
+  int e[2];
+  float2 wt[2][4];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const CellPairs &a = p == 0 ? a0 : a1;
+    const RotPairs &rot = p == 0 ? rot0 : rot1;
+    float2 d = __fmul2_rn(a.a00, lo2(q00));
+    float2 w = __fmul2_rn(a.a00, hi2(q00));
+    d = __ffma2_rn(a.a10, lo2(q10), d);
+    w = __ffma2_rn(a.a10, hi2(q10), w);
+    if (DIMS == 2) {
+      d = __ffma2_rn(a.a01, lo2(q01), d);
+      w = __ffma2_rn(a.a01, hi2(q01), w);
+      d = __ffma2_rn(a.a11, lo2(q11), d);
+      w = __ffma2_rn(a.a11, hi2(q11), w);
+    }
+    if (ROT) d = __ffma2_rn(make_float2(d.x, d.x), rot.c, __fmul2_rn(make_float2(d.y, d.y), rot.s));
+    // split and bounds as in sv_tap
+    const float magic = 12582912.0f;
+    const float2 r = __fadd2_rn(__fadd2_rn(d, make_float2(-0.5f, -0.5f)), make_float2(magic, magic));
+    const float2 f = __ffma2_rn(__fadd2_rn(r, make_float2(-magic, -magic)), make_float2(-1.f, -1.f), d);
+    const int nx = __float_as_int(r.x) - 0x4B400000;
+    const int ny = __float_as_int(r.y) - 0x4B400000;
+    e[p] = base0 + p * RW + ny * RW + nx;
+    const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y);
+    const float2 wy1 = __fmul2_rn(w, fy), wy0 = __ffma2_rn(wy1, make_float2(-1.f, -1.f), w);
+    wt[p][3] = __fmul2_rn(wy1, fx);
+    wt[p][2] = __ffma2_rn(wt[p][3], make_float2(-1.f, -1.f), wy1);
+    wt[p][1] = __fmul2_rn(wy0, fx);
+    wt[p][0] = __ffma2_rn(wt[p][1], make_float2(-1.f, -1.f), wy0);
+  }
+  // upper pixel: four corners
+  const float2 rg00 = st.rg[e[0]], rg01 = st.rg[e[0] + 1];
+  const float2 rg10 = st.rg[e[0] + RW], rg11 = st.rg[e[0] + RW + 1];
+  float2 ba00, ba01, ba10, ba11;
+  if (CH == 4) {
+    ba00 = st.ba[e[0]]; ba01 = st.ba[e[0] + 1]; ba10 = st.ba[e[0] + RW]; ba11 = st.ba[e[0] + RW + 1];
+  } else {
+    ba00 = make_float2(st.b[e[0]], 0.f); ba01 = make_float2(st.b[e[0] + 1], 0.f);
+    ba10 = make_float2(st.b[e[0] + RW], 0.f); ba11 = make_float2(st.b[e[0] + RW + 1], 0.f);
+  }
+  auto accum = [&](Acc &acc, const float2 &wb, const float2 &rg, const float2 &ba) {
+    acc.rg = __ffma2_rn(wb, rg, acc.rg);
+    acc.b = fmaf(wb.x, ba.x, acc.b);
+    if (CH == 4) acc.a = fmaf(wb.x, ba.y, acc.a);
+  };
+  accum(acc0, wt[0][0], rg00, ba00);
+  accum(acc0, wt[0][1], rg01, ba01);
+  accum(acc0, wt[0][2], rg10, ba10);
+  accum(acc0, wt[0][3], rg11, ba11);
+  // lower pixel: its top row is the upper pixel's bottom row when the
+  // integer offsets agree (e[1] == e[0] + RW)
+  const bool reuse = e[1] == e[0] + RW;
+  float2 t0, t1, tb0, tb1;
+  if (reuse) {
+    t0 = rg10; t1 = rg11; tb0 = ba10; tb1 = ba11;
+  } else {
+    t0 = st.rg[e[1]]; t1 = st.rg[e[1] + 1];
+    if (CH == 4) { tb0 = st.ba[e[1]]; tb1 = st.ba[e[1] + 1]; }
+    else { tb0 = make_float2(st.b[e[1]], 0.f); tb1 = make_float2(st.b[e[1] + 1], 0.f); }
+  }
+  accum(acc1, wt[1][0], t0, tb0);
+  accum(acc1, wt[1][1], t1, tb1);
+  const float2 u0 = st.rg[e[1] + RW], u1 = st.rg[e[1] + RW + 1];
+  float2 ub0, ub1;
+  if (CH == 4) { ub0 = st.ba[e[1] + RW]; ub1 = st.ba[e[1] + RW + 1]; }
+  else { ub0 = make_float2(st.b[e[1] + RW], 0.f); ub1 = make_float2(st.b[e[1] + RW + 1], 0.f); }
+  accum(acc1, wt[1][2], u0, ub0);
+  accum(acc1, wt[1][3], u1, ub1);
+}
+
 template <int DIMS, int SRC, int DST, int TAPS, int CH, int PIX, bool ROT>
 __global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : 3)
 sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
@@ -266,7 +348,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   float2 rv[kSvPix];
 #pragma unroll
   for (int j = 0; j < kSvPix; ++j) {
-    const int yc = min(ty0 + warp + kSvWarps * j, P.H - 1);
+    const int yc = min(ty0 + warp * kSvPix + j, P.H - 1);
     const long long px = (long long)yc * P.W + xc;
     pv0[j] = __ldg(P.maps + px);
     pv1[j] = DIMS == 2 ? __ldg(P.maps + HW + px) : 0.f;
@@ -352,7 +434,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
     c[j] = make_cell_v<DIMS>(P.ax, pv0[j], pv1[j]);
     cp[j] = cell_pairs(c[j]);
     rp[j] = {rv[j], make_float2(-rv[j].y, rv[j].x)};
-    base[j] = (warp + kSvWarps * j + halo) * RW + (lane + hx);
+    base[j] = (warp * kSvPix + j + halo) * RW + (lane + hx);
     acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
     same = same && (c[j].n00 == c[0].n00);
   }
@@ -399,8 +481,9 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
         const float4 q01 = DIMS == 2 ? fetch(b01 + i) : q00;
         const float4 q11 = DIMS == 2 ? fetch(b11 + i) : q10;
 #pragma unroll
-        for (int j = 0; j < kSvPix; ++j)
-          sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
+        for (int j = 0; j < kSvPix; j += 2)
+          sv_tap_pair<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], cp[j + 1], rp[j], rp[j + 1], st,
+                                     base[j], RW, acc[j], acc[j + 1]);
       }
     } else {
       // unrolled so the per-pixel arrays stay in registers
@@ -426,7 +509,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   if (x < P.W) {
 #pragma unroll
     for (int j = 0; j < kSvPix; ++j) {
-      const int y = ty0 + warp + kSvWarps * j;
+      const int y = ty0 + warp * kSvPix + j;
       if (y < P.H) {
         const float4 v = make_float4(acc[j].rg.x, acc[j].rg.y, acc[j].b, acc[j].a);
         if (DST == PIX_PLANAR)
