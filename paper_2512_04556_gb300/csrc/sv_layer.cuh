@@ -2,7 +2,7 @@
 // Eq. 3): the kernel template shared by the 1-D and 2-D translation units.
 //
 // Each CTA owns a 32 x 16 or 32 x 32 output tile (PIX = 2 or 4 vertically
-// adjacent pixels of one column per thread; a pair of them shares the
+// adjacent pixels of one column per thread; neighbouring pixels share the
 // corner row between them when their integer offsets agree).  It stages the layer's source
 // region (tile + the layer's halo, clamp-to-edge) into shared memory as FP32
 // planes -- (r, g) pairs in one, b (or (b, a) pairs) in another -- converting
@@ -208,22 +208,29 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
   add_corner<CH>(st, e + RW + 1, w11, acc);
 }
 
-// Two vertically adjacent pixels of one thread and one tap.  Their sample
-// points usually have the same integer offset (the offsets vary slowly
-// across pixels), and then the lower pixel's top corners are the upper
-// pixel's bottom corners: they are read from shared memory once.
-template <int DIMS, int CH, bool ROT>
-__device__ __forceinline__ void sv_tap_pair(const float4 &q00, const float4 &q10, const float4 &q01,
-                                            const float4 &q11, const CellPairs &a0,
-                                            const CellPairs &a1, const RotPairs &rot0,
-                                            const RotPairs &rot1, const Staged &st, int base0, int RW,
-                                            Acc &acc0, Acc &acc1) {
-  int e[2];
-  float2 wt[2][4];
+// The thread's N vertically adjacent pixels and one tap, top to bottom.
+// Neighbouring pixels' sample points usually have the same integer offset
+// (the offsets vary slowly across pixels), and then a pixel's top corners
+// are the previous pixel's bottom corners: they are kept in registers
+// instead of being read from shared memory again.
+template <int DIMS, int CH, bool ROT, int N>
+__device__ __forceinline__ void sv_tap_column(const float4 &q00, const float4 &q10, const float4 &q01,
+                                              const float4 &q11, const CellPairs *cp,
+                                              const RotPairs *rp, const Staged &st, int base0,
+                                              int RW, Acc *acc) {
+  int eprev = 0;
+  float2 prg0 = make_float2(0.f, 0.f), prg1 = prg0, pba0 = prg0, pba1 = prg0;
+  auto accum = [&](Acc &a, const float2 &wb, const float2 &rg, const float2 &ba) {
+    a.rg = __ffma2_rn(wb, rg, a.rg);
+    a.b = fmaf(wb.x, ba.x, a.b);
+    if (CH == 4) a.a = fmaf(wb.x, ba.y, a.a);
+  };
+  auto load_ba = [&](int e) -> float2 {
+    return CH == 4 ? st.ba[e] : make_float2(st.b[e], 0.f);
+  };
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    const CellPairs &a = p == 0 ? a0 : a1;
-    const RotPairs &rot = p == 0 ? rot0 : rot1;
+  for (int p = 0; p < N; ++p) {
+    const CellPairs &a = cp[p];
     float2 d = __fmul2_rn(a.a00, lo2(q00));
     float2 w = __fmul2_rn(a.a00, hi2(q00));
     d = __ffma2_rn(a.a10, lo2(q10), d);
@@ -234,59 +241,32 @@ __device__ __forceinline__ void sv_tap_pair(const float4 &q00, const float4 &q10
       d = __ffma2_rn(a.a11, lo2(q11), d);
       w = __ffma2_rn(a.a11, hi2(q11), w);
     }
-    if (ROT) d = __ffma2_rn(make_float2(d.x, d.x), rot.c, __fmul2_rn(make_float2(d.y, d.y), rot.s));
+    if (ROT) d = __ffma2_rn(make_float2(d.x, d.x), rp[p].c, __fmul2_rn(make_float2(d.y, d.y), rp[p].s));
     // split and bounds as in sv_tap
     const float magic = 12582912.0f;
     const float2 r = __fadd2_rn(__fadd2_rn(d, make_float2(-0.5f, -0.5f)), make_float2(magic, magic));
     const float2 f = __ffma2_rn(__fadd2_rn(r, make_float2(-magic, -magic)), make_float2(-1.f, -1.f), d);
     const int nx = __float_as_int(r.x) - 0x4B400000;
     const int ny = __float_as_int(r.y) - 0x4B400000;
-    e[p] = base0 + p * RW + ny * RW + nx;
+    const int e = base0 + p * RW + ny * RW + nx;
     const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y);
     const float2 wy1 = __fmul2_rn(w, fy), wy0 = __ffma2_rn(wy1, make_float2(-1.f, -1.f), w);
-    wt[p][3] = __fmul2_rn(wy1, fx);
-    wt[p][2] = __ffma2_rn(wt[p][3], make_float2(-1.f, -1.f), wy1);
-    wt[p][1] = __fmul2_rn(wy0, fx);
-    wt[p][0] = __ffma2_rn(wt[p][1], make_float2(-1.f, -1.f), wy0);
+    const float2 w11 = __fmul2_rn(wy1, fx), w10 = __ffma2_rn(w11, make_float2(-1.f, -1.f), wy1);
+    const float2 w01 = __fmul2_rn(wy0, fx), w00 = __ffma2_rn(w01, make_float2(-1.f, -1.f), wy0);
+    float2 t0, t1, tb0, tb1;
+    if (p > 0 && e == eprev + RW) {
+      t0 = prg0; t1 = prg1; tb0 = pba0; tb1 = pba1;
+    } else {
+      t0 = st.rg[e]; t1 = st.rg[e + 1]; tb0 = load_ba(e); tb1 = load_ba(e + 1);
+    }
+    prg0 = st.rg[e + RW]; prg1 = st.rg[e + RW + 1];
+    pba0 = load_ba(e + RW); pba1 = load_ba(e + RW + 1);
+    eprev = e;
+    accum(acc[p], w00, t0, tb0);
+    accum(acc[p], w01, t1, tb1);
+    accum(acc[p], w10, prg0, pba0);
+    accum(acc[p], w11, prg1, pba1);
   }
-  // upper pixel: four corners
-  const float2 rg00 = st.rg[e[0]], rg01 = st.rg[e[0] + 1];
-  const float2 rg10 = st.rg[e[0] + RW], rg11 = st.rg[e[0] + RW + 1];
-  float2 ba00, ba01, ba10, ba11;
-  if (CH == 4) {
-    ba00 = st.ba[e[0]]; ba01 = st.ba[e[0] + 1]; ba10 = st.ba[e[0] + RW]; ba11 = st.ba[e[0] + RW + 1];
-  } else {
-    ba00 = make_float2(st.b[e[0]], 0.f); ba01 = make_float2(st.b[e[0] + 1], 0.f);
-    ba10 = make_float2(st.b[e[0] + RW], 0.f); ba11 = make_float2(st.b[e[0] + RW + 1], 0.f);
-  }
-  auto accum = [&](Acc &acc, const float2 &wb, const float2 &rg, const float2 &ba) {
-    acc.rg = __ffma2_rn(wb, rg, acc.rg);
-    acc.b = fmaf(wb.x, ba.x, acc.b);
-    if (CH == 4) acc.a = fmaf(wb.x, ba.y, acc.a);
-  };
-  accum(acc0, wt[0][0], rg00, ba00);
-  accum(acc0, wt[0][1], rg01, ba01);
-  accum(acc0, wt[0][2], rg10, ba10);
-  accum(acc0, wt[0][3], rg11, ba11);
-  // lower pixel: its top row is the upper pixel's bottom row when the
-  // integer offsets agree (e[1] == e[0] + RW)
-  const bool reuse = e[1] == e[0] + RW;
-  float2 t0, t1, tb0, tb1;
-  if (reuse) {
-    t0 = rg10; t1 = rg11; tb0 = ba10; tb1 = ba11;
-  } else {
-    t0 = st.rg[e[1]]; t1 = st.rg[e[1] + 1];
-    if (CH == 4) { tb0 = st.ba[e[1]]; tb1 = st.ba[e[1] + 1]; }
-    else { tb0 = make_float2(st.b[e[1]], 0.f); tb1 = make_float2(st.b[e[1] + 1], 0.f); }
-  }
-  accum(acc1, wt[1][0], t0, tb0);
-  accum(acc1, wt[1][1], t1, tb1);
-  const float2 u0 = st.rg[e[1] + RW], u1 = st.rg[e[1] + RW + 1];
-  float2 ub0, ub1;
-  if (CH == 4) { ub0 = st.ba[e[1] + RW]; ub1 = st.ba[e[1] + RW + 1]; }
-  else { ub0 = make_float2(st.b[e[1] + RW], 0.f); ub1 = make_float2(st.b[e[1] + RW + 1], 0.f); }
-  accum(acc1, wt[1][2], u0, ub0);
-  accum(acc1, wt[1][3], u1, ub1);
 }
 
 template <int DIMS, int SRC, int DST, int TAPS, int CH, int PIX, bool ROT>
@@ -480,10 +460,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
         const float4 q00 = fetch(b00 + i), q10 = fetch(b10 + i);
         const float4 q01 = DIMS == 2 ? fetch(b01 + i) : q00;
         const float4 q11 = DIMS == 2 ? fetch(b11 + i) : q10;
-#pragma unroll
-        for (int j = 0; j < kSvPix; j += 2)
-          sv_tap_pair<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], cp[j + 1], rp[j], rp[j + 1], st,
-                                     base[j], RW, acc[j], acc[j + 1]);
+        sv_tap_column<DIMS, CH, ROT, kSvPix>(q00, q10, q01, q11, cp, rp, st, base[0], RW, acc);
       }
     } else {
       // unrolled so the per-pixel arrays stay in registers
