@@ -179,6 +179,9 @@ extern "C" int disk_basis_from_arrays(int dims, const int *n_nodes, const float 
         taps[((size_t)l * b->B + k) * T + i] = make_float4(t[0], t[1], t[2], t[2]);
       }
   DISK_TRY_CUDA(cudaGetDevice(&b->device), "cudaGetDevice");
+  // the device status word the filter kernels report to, allocated now so
+  // that no later call (possibly inside a graph capture) has to
+  if (!disk::device_error_word()) return fail(DISK_ERR_CUDA, "device status word allocation failed");
   DISK_TRY_CUDA(cudaMalloc(&b->d_taps, taps.size() * sizeof(float4)), "cudaMalloc(basis)");
   cudaError_t e = cudaMemcpy(b->d_taps, taps.data(), taps.size() * sizeof(float4),
                              cudaMemcpyHostToDevice);
