@@ -396,6 +396,19 @@ int disk_mlp_train_step(float *d_params, float *d_m, float *d_v, int step,
                         const float *d_x, const float *d_target, int batch,
                         float *d_loss, void *stream);
 
+/* The two halves of disk_mlp_train_step, for data-parallel training (each
+ * rank computes the gradient of its own batch, the ranks average the
+ * gradients with one all-reduce, every rank applies the same update):
+ * disk_mlp_grad writes the loss of the batch (mean squared error, device
+ * float) and its gradient d_grad (one float per parameter, layout of the
+ * parameters); disk_mlp_adam applies one Adam update with that gradient
+ * (as disk_mlp_train_step; step counted from 1). */
+int disk_mlp_grad(const float *d_params, int n_in, int hidden, int depth, int n_out,
+                  const float *d_x, const float *d_target, int batch, float *d_grad,
+                  float *d_loss, void *stream);
+int disk_mlp_adam(float *d_params, float *d_m, float *d_v, const float *d_grad, int step,
+                  float lr, int n_in, int hidden, int depth, int n_out, void *stream);
+
 /* Area resampling of `batch` packed targets (as for disk_fit; sizes host
  * int[batch], <= 4096) to d_out [batch][side][side], each scaled to a
  * maximum of 1: output cell (j, i) averages the input pixels it overlaps,

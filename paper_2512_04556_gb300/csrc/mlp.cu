@@ -279,23 +279,19 @@ extern "C" int disk_mlp_forward(const float *d_params, int n_in, int hidden, int
   return rc;
 }
 
-extern "C" int disk_mlp_train_step(float *d_params, float *d_m, float *d_v, int step, float lr,
-                                   int n_in, int hidden, int depth, int n_out, const float *d_x,
-                                   const float *d_target, int batch, float *d_loss, void *stream) {
-  const Shape sh{n_in, hidden, depth, n_out};
-  int rc = check_shape(sh);
-  if (rc) return rc;
-  if (!d_params || !d_m || !d_v || !d_x || !d_target || !d_loss || batch < 1 || step < 1)
-    return fail(DISK_ERR_INVALID_ARG, "bad arguments");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const long long np = sh.count();
-  const long long nacts = (long long)batch * sh.hidden * sh.depth, ny = (long long)batch * n_out;
-  const long long wmax = std::max(sh.hidden, n_out);
-  const size_t bytes = sizeof(float) * (nacts + ny + 2 * batch * wmax + np);
+namespace disk {
+namespace {
+
+// Loss and gradient of one batch into grad (np floats); scratch from the pool.
+int mlp_grad(const Shape &sh, const float *d_params, const float *d_x, const float *d_target,
+             int batch, float *grad, float *d_loss, cudaStream_t s) {
+  const long long nacts = (long long)batch * sh.hidden * sh.depth, ny = (long long)batch * sh.n_out;
+  const long long wmax = std::max(sh.hidden, sh.n_out);
+  const size_t bytes = sizeof(float) * (nacts + ny + 2 * batch * wmax);
   float *buf = nullptr;
-  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&buf), bytes, s), "scratch_alloc(mlp train)");
-  float *acts = buf, *y = acts + nacts, *d0 = y + ny, *d1 = d0 + batch * wmax, *grad = d1 + batch * wmax;
-  rc = mlp_forward(sh, d_params, d_x, batch, y, acts, nullptr, s);
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&buf), bytes, s), "scratch_alloc(mlp grad)");
+  float *acts = buf, *y = acts + nacts, *d0 = y + ny, *d1 = d0 + batch * wmax;
+  int rc = mlp_forward(sh, d_params, d_x, batch, y, acts, nullptr, s);
   cudaError_t e = cudaSuccess;
   if (rc == DISK_OK) {
     e = cudaMemsetAsync(d_loss, 0, sizeof(float), s);
@@ -322,14 +318,62 @@ extern "C" int disk_mlp_train_step(float *d_params, float *d_m, float *d_v, int 
       float *t = d; d = dn; dn = t;
     }
   }
-  if (rc == DISK_OK) {
-    const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
-    adam_kernel<<<1216, 256, 0, s>>>(d_params, d_m, d_v, grad, np, lr, c1, c2);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) rc = cuda_fail(e, "adam");
-  }
   cudaFreeAsync(buf, s);
   return rc;
+}
+
+int mlp_adam(long long np, float *d_params, float *d_m, float *d_v, const float *grad, int step,
+             float lr, cudaStream_t s) {
+  const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
+  adam_kernel<<<1216, 256, 0, s>>>(d_params, d_m, d_v, grad, np, lr, c1, c2);
+  DISK_TRY_CUDA(cudaGetLastError(), "adam");
+  return DISK_OK;
+}
+
+}  // namespace
+}  // namespace disk
+
+extern "C" int disk_mlp_train_step(float *d_params, float *d_m, float *d_v, int step, float lr,
+                                   int n_in, int hidden, int depth, int n_out, const float *d_x,
+                                   const float *d_target, int batch, float *d_loss, void *stream) {
+  const Shape sh{n_in, hidden, depth, n_out};
+  int rc = check_shape(sh);
+  if (rc) return rc;
+  if (!d_params || !d_m || !d_v || !d_x || !d_target || !d_loss || batch < 1 || step < 1)
+    return fail(DISK_ERR_INVALID_ARG, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long np = sh.count();
+  float *grad = nullptr;
+  DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&grad), sizeof(float) * np, s),
+                "scratch_alloc(mlp train)");
+  rc = mlp_grad(sh, d_params, d_x, d_target, batch, grad, d_loss, s);
+  if (rc == DISK_OK) rc = mlp_adam(np, d_params, d_m, d_v, grad, step, lr, s);
+  cudaFreeAsync(grad, s);
+  return rc;
+}
+
+extern "C" int disk_mlp_grad(const float *d_params, int n_in, int hidden, int depth, int n_out,
+                             const float *d_x, const float *d_target, int batch, float *d_grad,
+                             float *d_loss, void *stream) {
+  const Shape sh{n_in, hidden, depth, n_out};
+  int rc = check_shape(sh);
+  if (rc) return rc;
+  if (!d_params || !d_x || !d_target || !d_grad || !d_loss || batch < 1)
+    return fail(DISK_ERR_INVALID_ARG, "bad arguments");
+  return mlp_grad(sh, d_params, d_x, d_target, batch, d_grad, d_loss,
+                  static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int disk_mlp_adam(float *d_params, float *d_m, float *d_v, const float *d_grad,
+                             int step, float lr, int n_in, int hidden, int depth, int n_out,
+                             void *stream) {
+  const Shape sh{n_in, hidden, depth, n_out};
+  int rc = check_shape(sh);
+  if (rc) return rc;
+  if (!d_params || !d_m || !d_v || !d_grad || step < 1)
+    return fail(DISK_ERR_INVALID_ARG, "bad arguments");
+  return mlp_adam(sh.count(), d_params, d_m, d_v, d_grad, step, lr,
+                  static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int disk_downsample_targets(const float *d_targets, const int *sizes, int batch,

@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
             "disk_mlp_train_step": (_i, [_vp, _vp, _vp, _i, ctypes.c_float, _i, _i, _i, _i, _vp, _vp,
                                          _i, _vp, _vp]),
             "disk_downsample_targets": (_i, [_vp, _ip, _i, _i, _vp, _vp]),
+            "disk_mlp_grad": (_i, [_vp, _i, _i, _i, _i, _vp, _vp, _i, _vp, _vp, _vp]),
+            "disk_mlp_adam": (_i, [_vp, _vp, _vp, _vp, _i, ctypes.c_float, _i, _i, _i, _i, _vp]),
             "disk_fit_loss_grad": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _vp,
                                         _vp]),
         }
@@ -495,6 +497,23 @@ class MLP:
             _vp(self.params.data_ptr()), *self.shape, _vp(x.data_ptr()), x.shape[0],
             _vp(y.data_ptr()), _stream(stream)))
         return y
+
+    def grad(self, x, target, stream=None):
+        """(loss, gradient) of the batch without updating; both device tensors."""
+        import torch
+        g = torch.empty_like(self.params)
+        loss = torch.zeros(1, device=self.params.device, dtype=torch.float32)
+        _check("disk_mlp_grad", lib().disk_mlp_grad(
+            _vp(self.params.data_ptr()), *self.shape, _vp(x.data_ptr()), _vp(target.data_ptr()),
+            x.shape[0], _vp(g.data_ptr()), _vp(loss.data_ptr()), _stream(stream)))
+        return loss, g
+
+    def apply(self, grad, lr: float, stream=None):
+        """One Adam step with a given gradient (e.g. averaged over ranks)."""
+        self.step += 1
+        _check("disk_mlp_adam", lib().disk_mlp_adam(
+            _vp(self.params.data_ptr()), _vp(self.m.data_ptr()), _vp(self.v.data_ptr()),
+            _vp(grad.data_ptr()), self.step, lr, *self.shape, _stream(stream)))
 
     def train_step(self, x, target, lr: float, stream=None):
         """One Adam step on the batch; returns the loss as a device tensor."""

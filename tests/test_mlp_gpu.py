@@ -73,3 +73,29 @@ def test_learned_initializer_gains_over_the_radial_start(torch_cuda):
     res = li.evaluate(net, held_t, L, T, steps)
     assert res["median_iterations"] < steps, res
     assert res["median_start_loss_ratio"] < 1.0, res
+
+
+def test_grad_matches_oracle_and_halves_average_to_full_batch(torch_cuda):
+    """disk_mlp_grad against the FP64 gradient; the mean of two half-batch
+    gradients is the full-batch gradient (what the data-parallel all-reduce
+    relies on), and applying it equals one train_step on the full batch."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    shape = (64, 48, 2, 12)
+    g = np.random.default_rng(31)
+    x = g.random((40, 64)).astype(np.float32)
+    t = g.normal(size=(40, 12)).astype(np.float32)
+    a = disk.MLP(*shape, seed=9)
+    b = disk.MLP(*shape, seed=9)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    loss, grad = a.grad(xd, td)
+    wl_, wg = mlp.loss_and_grad(a.params.cpu().numpy().astype(np.float64), x, t, *shape)
+    assert abs(loss.item() - wl_) <= 1e-5 * abs(wl_)
+    assert np.abs(grad.cpu().numpy() - wg).max() <= 1e-5 * np.abs(wg).max()
+    _, g1 = a.grad(xd[:20], td[:20])
+    _, g2 = a.grad(xd[20:], td[20:])
+    avg = (g1 + g2) / 2
+    assert (avg - grad).abs().max().item() <= 1e-5 * grad.abs().max().item()
+    a.apply(avg, 1e-3)
+    b.train_step(xd, td, 1e-3)
+    assert (a.params - b.params).abs().max().item() <= 1e-6
