@@ -65,3 +65,20 @@ def filter_band(filter_fn, img, maps, band: Band):
     may be numpy arrays or tensors (any that slice like numpy)."""
     out = filter_fn(img[band.in_y0:band.in_y1], maps[:, band.in_y0:band.in_y1])
     return out[band.crop]
+
+
+def balance_targets(sizes, world: int) -> list[list[int]]:
+    """Split a batch of fitting targets over ranks (the fitter shards by
+    target, with no exchange): longest-processing-time greedy on a target's
+    work, taken as the area of its canvas (its size squared), so each rank's
+    total work is within one target's work of the others'."""
+    if world < 1:
+        raise ValueError("world >= 1 required")
+    order = sorted(range(len(sizes)), key=lambda i: (-int(sizes[i]) ** 2, i))
+    loads = [0] * world
+    parts: list[list[int]] = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (loads[k], k))
+        parts[r].append(i)
+        loads[r] += int(sizes[i]) ** 2
+    return parts

@@ -85,3 +85,13 @@ def test_two_ranks_gather_bands_gloo(tmp_path):
     full = oracle.sv_filter(img, maps, nn, nv, th)
     for r in range(2):
         np.testing.assert_array_equal(np.load(tmp_path / f"r{r}.npy"), full)
+
+
+def test_balance_targets_covers_and_balances():
+    sizes = [int(s) for s in np.random.default_rng(2).integers(16, 65, 257) * 2 + 1]
+    for world in (1, 2, 3, 8):
+        parts = shard.balance_targets(sizes, world)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(len(sizes)))
+        loads = [sum(sizes[i] ** 2 for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(s ** 2 for s in sizes)
