@@ -306,7 +306,6 @@ sv_theta_grad_kernel(const __grid_constant__ TgParams P) {
           v[9] += cj.a11 * t.x; v[10] += cj.a11 * t.y; v[11] += cj.a11 * t.z;
         }
       }
-#pragma unroll
       // reduce the 12 (2-D) or 6 (1-D) node-gradient values over the warp
       // in one reduce-scatter; one lane per value then adds it
       constexpr int NV = DIMS == 2 ? 16 : 8;

@@ -31,19 +31,15 @@ __global__ void rotation_kernel(const float *__restrict__ angle, float2 *__restr
 }
 
 int launch_layer(int dims, bool shared_taps, bool rot, int src, int dst, int C,
-                        const SvLayerParams &P, cudaStream_t s, int pix) {
-  if (dims == 1) {
-    if (rot)
-      return shared_taps ? launch_sv_layer<1, kSvTapsShared, true>(src, dst, C, P, s, pix)
-                         : launch_sv_layer<1, kSvTapsGlobal, true>(src, dst, C, P, s, pix);
-    return shared_taps ? launch_sv_layer<1, kSvTapsShared, false>(src, dst, C, P, s, pix)
-                       : launch_sv_layer<1, kSvTapsGlobal, false>(src, dst, C, P, s, pix);
-  }
-  if (rot)
-    return shared_taps ? launch_sv_layer<2, kSvTapsShared, true>(src, dst, C, P, s, pix)
-                       : launch_sv_layer<2, kSvTapsGlobal, true>(src, dst, C, P, s, pix);
-  return shared_taps ? launch_sv_layer<2, kSvTapsShared, false>(src, dst, C, P, s, pix)
-                     : launch_sv_layer<2, kSvTapsGlobal, false>(src, dst, C, P, s, pix);
+                 const SvLayerParams &P, cudaStream_t s, int pix) {
+  // One instantiation serves both: with tap_cap == 0 its blocks read the
+  // taps from global memory.
+  (void)shared_taps;
+  if (dims == 1)
+    return rot ? launch_sv_layer<1, kSvTapsShared, true>(src, dst, C, P, s, pix)
+               : launch_sv_layer<1, kSvTapsShared, false>(src, dst, C, P, s, pix);
+  return rot ? launch_sv_layer<2, kSvTapsShared, true>(src, dst, C, P, s, pix)
+             : launch_sv_layer<2, kSvTapsShared, false>(src, dst, C, P, s, pix);
 }
 
 // Exercises the bounded wait of the tile copies: the block arms an

@@ -59,9 +59,10 @@ __host__ __device__ constexpr size_t sv_smem_bytes(size_t RN, int C) {
 constexpr long long kSvMaxWaitIters = 1ll << 22;
 
 struct SvLayerParams {
-  // Tensor maps of the planar source's two planes (used when use_tma).
-  alignas(64) CUtensorMap tm_a;
-  alignas(64) CUtensorMap tm_b;
+  // Tensor maps of the planar source's two planes (used when use_tma; the
+  // type carries the 128-byte alignment the copies require).
+  CUtensorMap tm_a;
+  CUtensorMap tm_b;
   const void *src;
   long long src_pitch;   // bytes per row (plane A's rows for a planar source)
   long long src_plane_b; // planar source: byte offset of plane B

@@ -3,5 +3,4 @@
 
 namespace disk {
 DISK_SV_INSTANTIATE(1, kSvTapsShared, false)
-DISK_SV_INSTANTIATE(1, kSvTapsGlobal, false)
 }  // namespace disk

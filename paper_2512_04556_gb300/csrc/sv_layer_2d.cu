@@ -3,5 +3,4 @@
 
 namespace disk {
 DISK_SV_INSTANTIATE(2, kSvTapsShared, false)
-DISK_SV_INSTANTIATE(2, kSvTapsGlobal, false)
 }  // namespace disk

@@ -3,5 +3,4 @@
 
 namespace disk {
 DISK_SV_INSTANTIATE(1, kSvTapsShared, true)
-DISK_SV_INSTANTIATE(1, kSvTapsGlobal, true)
 }  // namespace disk

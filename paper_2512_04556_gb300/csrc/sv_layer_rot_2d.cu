@@ -3,5 +3,4 @@
 
 namespace disk {
 DISK_SV_INSTANTIATE(2, kSvTapsShared, true)
-DISK_SV_INSTANTIATE(2, kSvTapsGlobal, true)
 }  // namespace disk
