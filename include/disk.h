@@ -117,11 +117,18 @@ void disk_basis_free(disk_basis *basis);
  *   not overlap.
  * d_maps: float [dims][H][W], dense, raw parameter values.
  * Limits: 1 <= H, W <= 32768; C in {3, 4}.
- * Intermediate layers are stored in the image's precision: FP32 RGBA for
- *   DISK_F32, FP16 RGBA (round to nearest even) for DISK_F16; arithmetic and
- *   accumulation are FP32 in both.
- * Scratch: 2 * H * W * E bytes (L >= 3) or H * W * E bytes (L = 2), E = 16
- *   (FP32) or 8 (FP16), from the stream's pool, freed on the stream. */
+ * Intermediate layers are stored in FP32 whatever the image precision, as
+ *   planes: (r, g) pairs and b (or (b, a) pairs), rows padded to a multiple
+ *   of 4 pixels; arithmetic and accumulation are FP32.  The output is
+ *   rounded to the image's precision (FP16 round to nearest even).
+ * Scratch: two intermediate buffers (one for L = 2, none for L = 1) of
+ *   about H * W * (C == 4 ? 16 : 12) bytes, plus, for the rotated variant,
+ *   an H * W * 8-byte (cos, sin) plane, from the library's memory pool,
+ *   freed on the stream.
+ * Tile configuration: the one disk_sv_filter_autotune recorded for this
+ *   frame shape, else 32 x 16 tiles.  Layers after the first have their tile
+ *   copied by the tensor-memory accelerator; a copy that does not complete
+ *   within its bounded wait is reported by disk_device_status. */
 int disk_sv_filter(const disk_basis *basis, const void *d_in, size_t in_pitch,
                    void *d_out, size_t out_pitch, int H, int W, int C,
                    int dtype, const float *d_maps, void *stream);
@@ -156,7 +163,7 @@ int disk_sv_filter_backward_image(const disk_basis *basis, const void *d_grad_ou
  * is stored by the forward call).  At an exact integer offset the derivative
  * is the one-sided one of the floor convention.  Floating-point atomics: the
  * last bits vary from run to run.  Scratch: (L-1) activation planes in the
- * image's precision plus two FP32 RGBA planes, from the stream's pool. */
+ * image's precision plus two FP32 RGBA planes, from the library's memory pool. */
 int disk_sv_filter_backward(const disk_basis *basis, const void *d_in, size_t in_pitch,
                             const void *d_grad_out, size_t gout_pitch, float *d_grad_in,
                             size_t gin_pitch, float *d_grad_theta, int H, int W, int C,
