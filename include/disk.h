@@ -9,12 +9,14 @@
  *     is queued; on an error nothing is launched and outputs are untouched.
  *   - Pointers prefixed d_ are device pointers on the current CUDA device;
  *     all other pointers are host pointers.  Every buffer is caller-owned;
- *     the library owns only disk_basis handles and per-call scratch, which it
- *     takes from the stream-ordered pool of the call's stream and returns on
- *     the same stream.
+ *     the library owns only disk_basis handles, a status word per device and
+ *     per-call scratch, which it takes stream-ordered from its own memory
+ *     pool on the current device (freed memory stays mapped for the next
+ *     call) and returns on the same stream.
  *   - stream is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Calls are asynchronous on that stream; no entry point
- *     synchronises the device except disk_basis_* (host<->device uploads).
+ *     synchronises the device except disk_basis_* (host<->device uploads),
+ *     the autotuners and disk_device_status.
  *   - Images are interleaved H x W x C (C = 3 or 4), row pitch in BYTES,
  *     element type DISK_F32 (float) or DISK_F16 (IEEE half).  Arithmetic is
  *     FP32 throughout; FP16 is a storage type only (inputs widened exactly,
@@ -144,7 +146,7 @@ int disk_sv_filter(const disk_basis *basis, const void *d_in, size_t in_pitch,
  * d_grad_out: H x W x C of type dtype (pitch in bytes); d_grad_in: H x W x C
  *   float (pitch in bytes, at least W * C * 4).  Other arguments as
  *   disk_sv_filter.  Scratch: two FP32 RGBA planes (2 * H * W * 16 bytes)
- *   from the stream's pool.  Accumulation uses floating-point atomics, so the
+ *   from the library's memory pool.  Accumulation uses floating-point atomics, so the
  *   last bits of the result vary from run to run. */
 int disk_sv_filter_backward_image(const disk_basis *basis, const void *d_grad_out,
                                   size_t gout_pitch, float *d_grad_in,
@@ -298,7 +300,7 @@ int disk_dense_sv(int dims, const int *n_nodes, const float *node_vals,
  * bounds every |dx|, |dy| of d_theta and sizes the canvases; a complex with a
  * tap beyond it (or a non-finite value) gets NaN in every output element.
  * Scratch: 2 * batch canvases of side 2 * ((K-1)/2 + L*(ceil(max_reach)+1)
- * + 1) + 1 floats from the stream's pool. */
+ * + 1) + 1 floats from the library's memory pool. */
 int disk_synth_kernel(const float *d_theta, int batch, int L, int T, int K,
                       float max_reach, float *d_out, void *stream);
 
@@ -331,7 +333,7 @@ int disk_synth_kernel(const float *d_theta, int batch, int L, int T, int K,
  * first.  Never synchronises, so a call can be captured in a CUDA graph.
  * Scratch:
  * (L+3) canvases of side 2*max((K_b-1)/2, (L+1)*(ceil(s_b)+1))+3 per target
- * from the stream's pool. */
+ * from the library's memory pool. */
 enum { DISK_LOSS_MSE = 0, DISK_LOSS_CHARB = 1 };
 enum { DISK_INIT_GIVEN = 0, DISK_INIT_IR = 1, DISK_INIT_SS = 2, DISK_INIT_RAND = 3 };
 
