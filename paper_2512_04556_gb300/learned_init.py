@@ -39,6 +39,8 @@ def fit_pairs(targets, L, T, steps, batch=1024, init=disk.INIT_IR, seed=0):
     thetas, losses = [], []
     for i in range(0, len(targets), batch):
         packed, sizes = disk.pack_targets(targets[i:i + batch])
+        if i == 0:
+            disk.fit_autotune(packed, sizes, L, T)  # launch configuration for this batch shape
         th, fl, _ = disk.fit(packed, sizes, L, T, steps, init=init, seed=seed)
         thetas.append(th)
         losses.append(fl)
