@@ -23,6 +23,11 @@ struct disk_basis {
   std::vector<float> reach_norm; // [L]: max over nodes, taps of sqrt(dx^2 + dy^2)
   int device = 0;
   float4 *d_taps = nullptr;      // [L][B][T] = (dx, dy, w, w)
+  // the same taps in the pair layout of the 3-channel filter (same shape;
+  // for each node, slot 2j = (dx_2j, dx_2j+1, dy_2j, dy_2j+1) and slot
+  // 2j + 1 = (w_2j, w_2j+1, w_2j, w_2j+1); an odd T's last slot as above);
+  // it shares d_taps' allocation
+  float4 *d_taps_pair = nullptr;
   // filter tile configuration (pixels per thread) of every layer, chosen by
   // disk_sv_filter_autotune per (H, W, C, dtype | rotated << 8); read by
   // disk_sv_filter and disk_sv_filter_rotated
@@ -63,6 +68,12 @@ inline int halo_of(float reach) {
 // when offsets are rotated at run time (a turned tap keeps its length).
 inline float layer_reach(const disk_basis *b, int l, bool rotated) {
   return rotated ? b->reach_norm[l] : b->reach[l];
+}
+
+// Layer l's node-tap table as the filter kernel for C channels reads it
+// (the pair layout for 3 channels).
+inline const float4 *layer_taps(const disk_basis *b, int l, int C) {
+  return (C == 3 ? b->d_taps_pair : b->d_taps) + (size_t)l * b->B * b->T;
 }
 
 // Kernel-space axis as the kernels see it: node values and inverse spacings.

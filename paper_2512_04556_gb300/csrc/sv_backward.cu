@@ -425,7 +425,6 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
   P.rot = nullptr;
   P.use_tma = 0;
   P.err = device_error_word();
-  P.src_plane_b = P.dst_plane_b = 0;
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16, mid = intermediate_kind(dtype);
@@ -437,7 +436,7 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
     P.src_pitch = l == 0 ? (long long)in_pitch : (long long)(W * mid_bytes);
     P.dst = planes[l];
     P.dst_pitch = (long long)(W * mid_bytes);
-    P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
+    P.gtaps = layer_taps(b, l, C);
     P.bt = b->B * b->T;
     const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(kSvDefaultPix) + 2 * P.halo), C);
     P.tap_cap = sv_tap_cap(b->dims, b->n_nodes[1], b->B, b->T, region);

@@ -15,45 +15,16 @@ enum PixKind : int {
   PIX_RGBA32 = 0,  // library intermediate for FP32 images: float4 per pixel, dense rows
   PIX_F32 = 1,     // caller image: C floats per pixel
   PIX_F16 = 2,     // caller image: C halves per pixel
-  PIX_RGBA16 = 3,  // library intermediate for FP16 images: 4 halves per pixel, dense rows
-  PIX_PLANAR = 4   // forward-filter intermediate: FP32 planes, see planar_* below
+  PIX_RGBA16 = 3   // library intermediate for FP16 images: 4 halves per pixel, dense rows
 };
 
-// FP32 planar intermediate of the forward filter (any image precision): an
-// (r, g) float2 plane, then a b float plane (3 channels) or (b, a) float2
-// plane (4 channels), both with rows of planar_pitch_px(W) pixels; plane B
-// starts at planar_plane_b(H, W) bytes (256-byte aligned).  The layout is
-// the shared-memory staging layout of the layer kernel, so a tile of it is
-// copied by the tensor-memory accelerator without conversion.
-__host__ __device__ inline long long planar_pitch_px(int W) { return (W + 3) & ~3; }
-__host__ __device__ inline size_t planar_plane_b(int H, int W) {
-  return ((size_t)H * planar_pitch_px(W) * 8 + 255) & ~(size_t)255;
-}
-__host__ __device__ inline size_t planar_bytes(int H, int W, int C) {
-  return planar_plane_b(H, W) + (size_t)H * planar_pitch_px(W) * (C == 4 ? 8 : 4);
-}
-
-// One pixel of a planar intermediate (row pitch of plane A pitch_a bytes).
-__device__ __forceinline__ float4 load_planar(const void *base, long long pitch_a, long long plane_b,
-                                              int C, int y, int x) {
-  const char *b = static_cast<const char *>(base);
-  const float2 rg = __ldg(reinterpret_cast<const float2 *>(b + (long long)y * pitch_a) + x);
-  if (C == 4) {
-    const float2 ba = __ldg(reinterpret_cast<const float2 *>(b + plane_b + (long long)y * pitch_a) + x);
-    return make_float4(rg.x, rg.y, ba.x, ba.y);
-  }
-  const float bb = __ldg(reinterpret_cast<const float *>(b + plane_b + (long long)y * (pitch_a / 2)) + x);
-  return make_float4(rg.x, rg.y, bb, 0.f);
-}
-
-__device__ __forceinline__ void store_planar(void *base, long long pitch_a, long long plane_b, int C,
-                                             int y, int x, float4 v) {
-  char *b = static_cast<char *>(base);
-  reinterpret_cast<float2 *>(b + (long long)y * pitch_a)[x] = make_float2(v.x, v.y);
-  if (C == 4)
-    reinterpret_cast<float2 *>(b + plane_b + (long long)y * pitch_a)[x] = make_float2(v.z, v.w);
-  else
-    reinterpret_cast<float *>(b + plane_b + (long long)y * (pitch_a / 2))[x] = v.z;
+// Row pitch of the forward filter's FP32 intermediates (any image
+// precision): C floats per pixel (the PIX_F32 layout), rows padded to 16
+// bytes.  The layout is the shared-memory staging layout of the layer
+// kernel, so a tile of it is copied by the tensor-memory accelerator without
+// conversion.
+__host__ __device__ inline long long f32_mid_pitch(int W, int C) {
+  return ((long long)W * C * 4 + 15) & ~15ll;
 }
 
 // Intermediate planes keep the caller's storage precision: FP32 RGBA for

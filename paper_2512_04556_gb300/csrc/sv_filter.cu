@@ -2,12 +2,12 @@
 // Eq. 3) as one shared-memory-staged launch per layer (kernel in
 // sv_layer.cuh); disk_sv_filter_rotated: the same with every pixel's taps
 // turned by a per-pixel angle (Sec. 5.3's rotational and radial blur).
-// Intermediate layers live in FP32 planar buffers (planar_* in
-// sv_common.cuh) from the library's memory pool; the first layer reads the
-// caller's image and the last writes the caller's output.  A layer that reads
-// a planar buffer has its source tile copied into shared memory by the
-// tensor-memory accelerator (one 2-D copy per plane, an mbarrier, a bounded
-// wait).
+// Intermediate layers live in FP32 buffers (C floats per pixel, rows
+// padded to 16 bytes; f32_mid_pitch in sv_common.cuh) from the library's
+// memory pool; the first layer reads the caller's image and the last writes
+// the caller's output.  A layer that reads an intermediate has its source
+// tile copied into shared memory by the tensor-memory accelerator (one 2-D
+// copy, an mbarrier, a bounded wait).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -63,25 +63,26 @@ __global__ void wait_selftest_kernel(int *err, long long iters) {
 namespace {
 
 // Staging geometry of layer l: halo rows above and below the tile, halo_x
-// columns left and right.  Layers after the first read a planar buffer,
-// which the tensor-memory accelerator copies when the copy's box fits its
-// 256-element limit (the (r, g) plane's box is 2 (32 + 2 halo_x) floats
-// wide); their halo_x is rounded up to a multiple of 4 pixels so that every
-// copy starts on a 16-byte boundary (tile origins are multiples of 32).
+// columns left and right.  Layers after the first read an FP32
+// intermediate, which the tensor-memory accelerator copies when the copy's
+// box fits its 256-element limit (rows of C (32 + 2 halo_x) floats, copied
+// as 8-byte elements: C (32 + 2 halo_x) / 2 <= 256); their halo_x is rounded
+// up to a multiple of 4 pixels so that every copy starts on a 16-byte
+// boundary (tile origins are multiples of 32).
 struct LayerGeom {
   int halo, halo_x, tma;
 };
 
-LayerGeom layer_geom(const disk_basis *b, int l, bool rot) {
+LayerGeom layer_geom(const disk_basis *b, int C, int l, bool rot) {
   const int h = halo_of(layer_reach(b, l, rot));
   if (l == 0) return {h, h, 0};
   const int hx = (h + 3) & ~3;
-  if (2 * (kSvTileW + 2 * hx) <= 256) return {h, hx, 1};
+  if (C * (kSvTileW + 2 * hx) / 2 <= 256) return {h, hx, 1};
   return {h, h, 0};
 }
 
 size_t layer_smem(const disk_basis *b, int C, int l, int pix, bool rot) {
-  const LayerGeom g = layer_geom(b, l, rot);
+  const LayerGeom g = layer_geom(b, C, l, rot);
   return sv_smem_bytes((size_t)(kSvTileW + 2 * g.halo_x) * (sv_tile_h(pix) + 2 * g.halo), C);
 }
 
@@ -103,15 +104,16 @@ EncodeTiled encode_tiled() {
   return fn;
 }
 
-// 2-D FP32 tensor map of one plane: width elements per row, rows of pitch
-// bytes, box_w x box_h elements per copy, zeros outside.
-bool encode_plane(EncodeTiled fn, CUtensorMap *m, const void *base, int width, int H,
-                  long long pitch, int box_w, int box_h) {
+// 2-D tensor map of an FP32 intermediate viewed as 8-byte elements (the
+// copy moves bytes; a pixel's C floats stay in order): width elements per
+// row, rows of pitch bytes, box_w x box_h elements per copy, zeros outside.
+bool encode_rows(EncodeTiled fn, CUtensorMap *m, const void *base, long long width, int H,
+                 long long pitch, int box_w, int box_h) {
   const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)H};
   const cuuint64_t strides[1] = {(cuuint64_t)pitch};
   const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
   const cuuint32_t es[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box,
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(base), dims, strides, box,
             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -128,14 +130,13 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   P.H = H; P.W = W; P.C = C; P.T = b->T;
   make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
   const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
-  const int mid = PIX_PLANAR;
-  const long long mid_pitch = planar_pitch_px(W) * 8;
-  const long long mid_plane_b = (long long)planar_plane_b(H, W);
+  const int mid = PIX_F32;
+  const long long mid_pitch = f32_mid_pitch(W, C);
   const int L = b->L;
   const bool rotated = d_angle != nullptr;
   const EncodeTiled encode = encode_tiled();
   void *bufs[2] = {nullptr, nullptr};
-  const size_t plane = planar_bytes(H, W, C);
+  const size_t plane = (size_t)H * mid_pitch;
   const int nbuf = L >= 3 ? 2 : (L == 2 ? 1 : 0);
   for (int i = 0; i < nbuf; ++i) {
     cudaError_t e = scratch_alloc(&bufs[i], plane, s);
@@ -162,7 +163,7 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
     if (e != cudaSuccess) rc = cuda_fail(e, "launch rotation_kernel");
   }
   for (int l = 0; l < L && rc == DISK_OK; ++l) {
-    const LayerGeom g = layer_geom(b, l, rotated);
+    const LayerGeom g = layer_geom(b, C, l, rotated);
     P.halo = g.halo;
     P.halo_x = g.halo_x;
     P.region_w = kSvTileW + 2 * g.halo_x;
@@ -170,18 +171,15 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
     const int dst = l == L - 1 ? user : mid;
     P.src = l == 0 ? d_in : bufs[(l - 1) & 1];
     P.src_pitch = l == 0 ? (long long)in_pitch : mid_pitch;
-    P.src_plane_b = l == 0 ? 0 : mid_plane_b;
     P.dst = l == L - 1 ? d_out : bufs[l & 1];
     P.dst_pitch = l == L - 1 ? (long long)out_pitch : mid_pitch;
-    P.dst_plane_b = l == L - 1 ? 0 : mid_plane_b;
     P.use_tma = 0;
     if (g.tma && encode) {
       const int RW = P.region_w, RH = sv_tile_h(pix[l]) + 2 * g.halo;
-      const char *base = static_cast<const char *>(P.src);
-      const bool ok =
-          encode_plane(encode, &P.tm_a, base, 2 * W, H, mid_pitch, 2 * RW, RH) &&
-          (C == 4 ? encode_plane(encode, &P.tm_b, base + mid_plane_b, 2 * W, H, mid_pitch, 2 * RW, RH)
-                  : encode_plane(encode, &P.tm_b, base + mid_plane_b, W, H, mid_pitch / 2, RW, RH));
+      // rows of ceil(C W / 2) eight-byte elements (for odd C W the last
+      // element's second half is row padding, inside the pitch)
+      const bool ok = encode_rows(encode, &P.tm, P.src, ((long long)C * W + 1) / 2, H, mid_pitch,
+                                  C * RW / 2, RH);
       if (ok) {
         P.use_tma = 1;
       } else {
@@ -191,7 +189,7 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
         P.region_w = kSvTileW + 2 * g.halo;
       }
     }
-    P.gtaps = b->d_taps + (size_t)l * b->B * b->T;
+    P.gtaps = layer_taps(b, l, C);
     P.bt = b->B * b->T;
     if (ev) cudaEventRecord(ev[l], s);
     const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(pix[l]) + 2 * P.halo), C);

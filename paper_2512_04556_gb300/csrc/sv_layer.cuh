@@ -3,19 +3,27 @@
 //
 // Each CTA owns a 32 x 16 or 32 x 32 output tile (PIX = 2 or 4 vertically
 // adjacent pixels of one column per thread; neighbouring pixels share the
-// corner row between them when their integer offsets agree).  It stages the layer's source
-// region (tile + the layer's halo, clamp-to-edge) into shared memory as FP32
-// planes -- (r, g) pairs in one, b (or (b, a) pairs) in another -- converting
-// FP16 sources once per staged pixel instead of once per tap and corner; a
-// warp's 32 lanes (consecutive columns) read consecutive entries.  A planar
-// FP32 intermediate is copied in by the tensor-memory accelerator; the
+// corner row between them when their integer offsets agree).  It stages the
+// layer's source region (tile + the layer's halo, clamp-to-edge) into shared
+// memory as FP32 pixels, C floats each, converting FP16 sources once per
+// staged pixel instead of once per tap and corner; a warp's 32 lanes
+// (consecutive columns) read consecutive pixels.  An FP32 intermediate
+// (16-byte aligned rows) is copied in by the tensor-memory accelerator; the
 // caller's image goes through registers.  The layer's node taps are copied
-// into shared memory beside the region.  Arithmetic and accumulation are FP32.
+// into shared memory beside the region.  Arithmetic and accumulation are
+// FP32.
 // When each thread's pixels sit in one kernel-space cell -- the common case,
 // parameter maps being smooth -- the node taps of each tap index are fetched
 // once per thread (128-bit shared-memory broadcasts) and blended for its
 // pixels with each pixel's own weights; warps with a thread whose pixels
 // straddle cells take the per-pixel path.
+// Three-channel images take the taps two at a time in packed FP32 pairs
+// (lane 0: tap i, lane 1: tap i + 1), from a copy of the table that stores
+// each pair's offsets and weights side by side: the blend, the floor split
+// and the corner weights then need no broadcast operands, and each channel
+// accumulates the even and the odd taps in the two lanes of one pair, summed
+// at the end.  Four-channel images take one tap at a time with (r, g) and
+// (b, a) as pairs.
 // The rotated variant (ROT) turns every pixel's blended tap offsets by that
 // pixel's angle before sampling: the runtime form of the rotational and
 // radial blur effects of Sec. 5.3, exact for the complex's impulse response.
@@ -42,15 +50,14 @@ __host__ __device__ constexpr int sv_tile_h(int pix) { return pix * kSvWarps; }
 enum : int { kSvTapsGlobal = 0, kSvTapsShared = 1 };
 constexpr int kSvMaxSmem = 232448;           // 227 KB opt-in shared memory per CTA
 
-// Shared-memory bytes per staged pixel: FP32 (r, g) + b, or (r, g) + (b, a).
-__host__ __device__ constexpr size_t sv_stage_bytes(int C) { return C == 4 ? 16 : 12; }
+// Shared-memory bytes per staged pixel: C FP32 values.
+__host__ __device__ constexpr size_t sv_stage_bytes(int C) { return (size_t)C * 4; }
 
-// Staged region of RN pixels: the (r, g) plane, then the b / (b, a) plane at
-// a 128-byte boundary (the tensor copies' destination alignment), then the
-// copy's mbarrier (8 bytes, in a 16-byte slot).
-__host__ __device__ constexpr size_t sv_plane_b_offset(size_t RN) { return (RN * 8 + 127) & ~(size_t)127; }
+// Staged region of RN pixels (C floats each, row-major, rows of region_w
+// pixels), then a 16-byte slot with the tile copy's mbarrier and the block's
+// node range.  The node taps follow.
 __host__ __device__ constexpr size_t sv_smem_bytes(size_t RN, int C) {
-  return ((sv_plane_b_offset(RN) + RN * (C == 4 ? 8 : 4) + 15) & ~(size_t)15) + 16;
+  return ((RN * sv_stage_bytes(C) + 15) & ~(size_t)15) + 16;
 }
 
 // Iteration limit of the wait for a tile copy (each try_wait may also
@@ -59,25 +66,25 @@ __host__ __device__ constexpr size_t sv_smem_bytes(size_t RN, int C) {
 constexpr long long kSvMaxWaitIters = 1ll << 22;
 
 struct SvLayerParams {
-  // Tensor maps of the planar source's two planes (used when use_tma; the
-  // type carries the 128-byte alignment the copies require).
-  CUtensorMap tm_a;
-  CUtensorMap tm_b;
+  // Tensor map of an FP32 source viewed as rows of 8-byte elements (used
+  // when use_tma; the type carries the 128-byte alignment the copies
+  // require).
+  CUtensorMap tm;
   const void *src;
-  long long src_pitch;   // bytes per row (plane A's rows for a planar source)
-  long long src_plane_b; // planar source: byte offset of plane B
+  long long src_pitch;   // bytes per row
   void *dst;
   long long dst_pitch;
-  long long dst_plane_b;
   const float *maps;
   const float2 *rot;    // [H][W] (cos, sin) of each pixel's angle, rotated variant only
-  const float4 *gtaps;  // [B][T] taps of this layer: (dx, dy, w, w)
+  // [B][T] taps of this layer: (dx, dy, w, w) per tap for 4 channels; for 3
+  // channels the pair layout of sv_pair_slots (sv_layer_taps picks).
+  const float4 *gtaps;
   int *err;             // device status word (DISK_ERR_TIMEOUT after a given-up wait)
   int H, W, C, T;
   int halo;             // rows staged above and below the tile
   int halo_x;           // columns staged left and right (>= halo; a multiple of 4 with TMA)
   int region_w;         // kSvTileW + 2 halo_x
-  int use_tma;          // planar source copied by the tensor-memory accelerator
+  int use_tma;          // FP32 source copied by the tensor-memory accelerator
   int bt;               // B * T taps of this layer
   int tap_cap;          // nodes whose taps a block may copy into shared memory
   AxisNodes ax[2];
@@ -89,7 +96,8 @@ __device__ __forceinline__ unsigned smem_addr(const void *p) {
 
 // One 2-D tile of a tensor map into shared memory, completing on mbarrier
 // bar (which expects the bytes beforehand).  x must be a multiple of 16
-// bytes' worth of elements; out-of-range elements read as zero.
+// bytes' worth of elements; out-of-range elements read as zero.  The source
+// rows are viewed as 8-byte elements (no conversion: the copy moves bytes).
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             unsigned bar) {
   asm volatile(
@@ -114,8 +122,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity,
   return false;
 }
 
-// Pixel weights of Eq. 9 broadcast into FP32 pairs for the packed
-// (f32x2) arithmetic of sv_tap; built once per pixel.
+// Pixel weights of Eq. 9 broadcast into FP32 pairs for the packed (f32x2)
+// arithmetic; built once per pixel.
 struct CellPairs {
   float2 a00, a10, a01, a11;
 };
@@ -125,49 +133,182 @@ __device__ __forceinline__ CellPairs cell_pairs(const Cell &c) {
           make_float2(c.a11, c.a11)};
 }
 
-// Per-pixel accumulator: (r, g) as a packed pair, b and a scalar.
+// Per-pixel accumulator, three FP32 pairs.  3 channels: r, g, b, each
+// (even taps, odd taps); 4 channels: (r, g), (b, a) and an unused pair.
 struct Acc {
-  float2 rg;
-  float b, a;
+  float2 p0, p1, p2;
 };
+
+template <int CH>
+__device__ __forceinline__ float4 acc_value(const Acc &a) {
+  if (CH == 3) return make_float4(a.p0.x + a.p0.y, a.p1.x + a.p1.y, a.p2.x + a.p2.y, 0.f);
+  return make_float4(a.p0.x, a.p0.y, a.p1.x, a.p1.y);
+}
 
 __device__ __forceinline__ float2 lo2(const float4 &v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(const float4 &v) { return make_float2(v.z, v.w); }
 
-// The staged region: (r, g) pairs, then b (3 channels) or (b, a) pairs.
-struct Staged {
-  const float2 *rg;
-  const float *b;     // CH == 3
-  const float2 *ba;   // CH == 4
-};
+// Floor split of an offset pair, both lanes at once: r = d + 1.5 * 2^23
+// rounded toward minus infinity is exactly floor(d) + 1.5 * 2^23 (|d| < 2^22,
+// where that sum's ulp is 1), so r's bit pattern minus kSvSplitBias is
+// floor(d); the fraction f = d - floor(d) in [0, 1) is exact.
+constexpr float kSvSplitMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr unsigned kSvSplitBias = 0x4B400000u; // bit pattern of kSvSplitMagic
+__device__ __forceinline__ float2 sv_split_floor(const float2 &d, float2 &f) {
+  const float2 r = __fadd2_rd(d, make_float2(kSvSplitMagic, kSvSplitMagic));
+  f = __ffma2_rn(__fadd2_rn(r, make_float2(-kSvSplitMagic, -kSvSplitMagic)), make_float2(-1.f, -1.f), d);
+  return r;
+}
 
-// Weighted corner e of the staged region into the accumulator.
-template <int CH>
-__device__ __forceinline__ void add_corner(const Staged &st, int e, const float2 &wb, Acc &acc) {
-  acc.rg = __ffma2_rn(wb, st.rg[e], acc.rg);
-  if (CH == 4) {
-    const float2 ba = st.ba[e];
-    acc.b = fmaf(wb.x, ba.x, acc.b);
-    acc.a = fmaf(wb.x, ba.y, acc.a);
-  } else {
-    acc.b = fmaf(wb.x, st.b[e], acc.b);
+// A region index with the split's bias folded in: sv_biased(b, RW) +
+// bits(ry) * RW + bits(rx) = b + floor(dy) * RW + floor(dx) (in wrapping
+// 32-bit arithmetic; the result is a valid index).
+__device__ __forceinline__ unsigned sv_biased(int base, int RW) {
+  return (unsigned)base - kSvSplitBias * (unsigned)(RW + 1);
+}
+__device__ __forceinline__ int sv_index(unsigned biased, int RW, float rx, float ry) {
+  return (int)(biased + (unsigned)__float_as_int(ry) * (unsigned)RW + (unsigned)__float_as_int(rx));
+}
+
+// Bilinear corner weights of a pair (per lane): w * (1 - fx) (1 - fy),
+// w fx (1 - fy), w (1 - fx) fy, w fx fy.
+struct CornerW {
+  float2 w00, w01, w10, w11;
+};
+__device__ __forceinline__ CornerW corner_weights(const float2 &w, const float2 &fx, const float2 &fy) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  CornerW c;
+  const float2 wy1 = __fmul2_rn(w, fy), wy0 = __ffma2_rn(wy1, m1, w);
+  c.w11 = __fmul2_rn(wy1, fx);
+  c.w10 = __ffma2_rn(c.w11, m1, wy1);
+  c.w01 = __fmul2_rn(wy0, fx);
+  c.w00 = __ffma2_rn(c.w01, m1, wy0);
+  return c;
+}
+
+// In bounds by construction: the Eq. 9 weights are non-negative and sum to
+// one within a few ulp (t is clamped to [0, 1] and p to the node range, NaN
+// to the first node), and every node tap satisfies |o| <= R, the layer
+// reach; so a blended |d| <= R (1 + 2^-21) and n = floor(d) lies in
+// [-ceil(R) - 1, ceil(R)] = [-halo, halo - 1], which with the corner n + 1
+// keeps every read inside the staged tile + halo region.  The rotated variant
+// takes R as the largest Euclidean tap length (the norm of a convex blend is
+// at most the largest node norm) and reads (cos, sin) normalised to unit
+// length by rotation_kernel, so each rotated component is within
+// R (1 + 2^-20): the same argument holds.
+
+// v + the four weighted corners, in the order top left, top right, bottom
+// left, bottom right.
+__device__ __forceinline__ float2 corners_into(float2 v, const CornerW &cw, const float2 &tl,
+                                               const float2 &tr, const float2 &bl, const float2 &br) {
+  v = __ffma2_rn(cw.w00, tl, v);
+  v = __ffma2_rn(cw.w01, tr, v);
+  v = __ffma2_rn(cw.w10, bl, v);
+  return __ffma2_rn(cw.w11, br, v);
+}
+
+// Offsets of the pair layout of a node's T taps (3-channel images): for
+// each j < T / 2, slot 2j holds (dx_2j, dx_2j+1, dy_2j, dy_2j+1) and slot
+// 2j + 1 holds (w_2j, w_2j+1, w_2j, w_2j+1); an odd T's last slot holds its
+// last tap as (dx, dy, w, w).
+
+// Eq. 9 blend of a tap pair's (dx, dy, w) for one pixel: lane 0 tap 2j,
+// lane 1 tap 2j + 1.
+template <int DIMS>
+__device__ __forceinline__ void blend_pair(const float4 (&A)[4], const float2 (&Wt)[4],
+                                           const CellPairs &a, float2 &dx, float2 &dy, float2 &w) {
+  dx = __fmul2_rn(a.a00, lo2(A[0]));
+  dy = __fmul2_rn(a.a00, hi2(A[0]));
+  w = __fmul2_rn(a.a00, Wt[0]);
+  dx = __ffma2_rn(a.a10, lo2(A[1]), dx);
+  dy = __ffma2_rn(a.a10, hi2(A[1]), dy);
+  w = __ffma2_rn(a.a10, Wt[1], w);
+  if (DIMS == 2) {
+    dx = __ffma2_rn(a.a01, lo2(A[2]), dx);
+    dy = __ffma2_rn(a.a01, hi2(A[2]), dy);
+    w = __ffma2_rn(a.a01, Wt[2], w);
+    dx = __ffma2_rn(a.a11, lo2(A[3]), dx);
+    dy = __ffma2_rn(a.a11, hi2(A[3]), dy);
+    w = __ffma2_rn(a.a11, Wt[3], w);
   }
 }
 
-// Rotation of a pixel's offsets as two pairs: (cos, sin) and (-sin, cos).
-struct RotPairs {
-  float2 c, s;
-};
+// (dx, dy) -> (dx cos - dy sin, dx sin + dy cos) for both lanes; rv =
+// (cos, sin) of the pixel.
+__device__ __forceinline__ void rotate_pair(const float2 &rv, float2 &dx, float2 &dy) {
+  const float2 c = make_float2(rv.x, rv.x), sn = make_float2(rv.y, rv.y);
+  const float2 x = __ffma2_rn(dx, c, __fmul2_rn(dy, make_float2(-rv.y, -rv.y)));
+  dy = __ffma2_rn(dx, sn, __fmul2_rn(dy, c));
+  dx = x;
+}
 
-// One tap of one pixel: the Eq. 9 blend of the node taps (dx, dy, w, w) with
-// the pixel's weights, the optional rotation of the blended offset, the
-// integer/fraction split of the offset, and the Eq. 2 bilinear sample from
-// the staged region, all in packed FP32 pairs: (dx, dy) and the corner
-// weights travel as pairs, colour as (r, g) + b.
+// A tap pair for the thread's N vertically adjacent pixels, top to bottom (3
+// channels; px: staged region, 3 floats per pixel).  Neighbouring pixels'
+// sample points usually have the same integer offset (the offsets vary
+// slowly across pixels), and then a pixel's top corners are the previous
+// pixel's bottom corners: they are kept in registers, per lane, instead of
+// being read from shared memory again.  Per channel the pair accumulates
+// corner by corner: top left, top right, bottom left, bottom right.
+template <int DIMS, bool ROT, int N>
+__device__ __forceinline__ void sv_pair_column(const float4 (&A)[4], const float2 (&Wt)[4],
+                                               const CellPairs *cp, const float2 *rv,
+                                               const float *px, int base0, int RW, Acc *acc) {
+  const unsigned biased0 = sv_biased(base0, RW);
+  int ep0 = 0, ep1 = 0;
+  // previous pixel's bottom row: channel k of the left (l) and right (r)
+  // corners, lanes (tap 2j, tap 2j + 1)
+  float2 bl[3], br[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) bl[k] = br[k] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int p = 0; p < N; ++p) {
+    float2 dx, dy, w;
+    blend_pair<DIMS>(A, Wt, cp[p], dx, dy, w);
+    if (ROT) rotate_pair(rv[p], dx, dy);
+    float2 fx, fy;
+    const float2 sx = sv_split_floor(dx, fx), sy = sv_split_floor(dy, fy);
+    const unsigned bp = biased0 + (unsigned)(p * RW);
+    const int e0 = sv_index(bp, RW, sx.x, sy.x), e1 = sv_index(bp, RW, sx.y, sy.y);
+    const CornerW cw = corner_weights(w, fx, fy);
+    const float *q0 = px + 3 * e0, *q1 = px + 3 * e1;
+    float2 tl[3], tr[3];
+    if (p > 0 && e0 == ep0 + RW) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { tl[k].x = bl[k].x; tr[k].x = br[k].x; }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { tl[k].x = q0[k]; tr[k].x = q0[3 + k]; }
+    }
+    if (p > 0 && e1 == ep1 + RW) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { tl[k].y = bl[k].y; tr[k].y = br[k].y; }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) { tl[k].y = q1[k]; tr[k].y = q1[3 + k]; }
+    }
+    const float *u0 = q0 + 3 * RW, *u1 = q1 + 3 * RW;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      bl[k] = make_float2(u0[k], u1[k]);
+      br[k] = make_float2(u0[3 + k], u1[3 + k]);
+    }
+    ep0 = e0;
+    ep1 = e1;
+    Acc &ac = acc[p];
+    ac.p0 = corners_into(ac.p0, cw, tl[0], tr[0], bl[0], br[0]);
+    ac.p1 = corners_into(ac.p1, cw, tl[1], tr[1], bl[1], br[1]);
+    ac.p2 = corners_into(ac.p2, cw, tl[2], tr[2], bl[2], br[2]);
+  }
+}
+
+// One tap (dx, dy, w, w blended from the four node taps q) for one pixel:
+// the last tap of an odd T for 3 channels (added to lane 0 of each channel
+// pair), or any tap for 4 channels ((r, g) and (b, a) pairs, px holding 4
+// floats per pixel).  Corner order as in sv_pair_column.
 template <int DIMS, int CH, bool ROT>
 __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, const float4 &q01,
-                                       const float4 &q11, const CellPairs &a, const RotPairs &rot,
-                                       const Staged &st, int base, int RW, Acc &acc) {
+                                       const float4 &q11, const CellPairs &a, const float2 &rv,
+                                       const float *px, int base, int RW, Acc &acc) {
   float2 d = __fmul2_rn(a.a00, lo2(q00));
   float2 w = __fmul2_rn(a.a00, hi2(q00));
   d = __ffma2_rn(a.a10, lo2(q10), d);
@@ -179,56 +320,40 @@ __device__ __forceinline__ void sv_tap(const float4 &q00, const float4 &q10, con
     w = __ffma2_rn(a.a11, hi2(q11), w);
   }
   // (dx, dy) -> (dx cos - dy sin, dx sin + dy cos)
-  if (ROT) d = __ffma2_rn(make_float2(d.x, d.x), rot.c, __fmul2_rn(make_float2(d.y, d.y), rot.s));
-  // integer part n = round-to-nearest(d - 1/2) (= floor(d) except at exact
-  // integers, where bilinear sampling gives the same value either way) and
-  // fraction f = d - n in [0, 1], for both axes at once; see split_offset.
-  const float magic = 12582912.0f;
-  const float2 r = __fadd2_rn(__fadd2_rn(d, make_float2(-0.5f, -0.5f)), make_float2(magic, magic));
-  const float2 f = __ffma2_rn(__fadd2_rn(r, make_float2(-magic, -magic)), make_float2(-1.f, -1.f), d);
-  // In bounds by construction: the Eq. 9 weights are non-negative and sum to
-  // one within a few ulp (t is clamped to [0, 1] and p to the node range,
-  // NaN to the first node), and every node tap satisfies |o| <= R, the layer
-  // reach; so the blended |d| <= R (1 + 2^-21) and n = round(d - 1/2) lies in
-  // [-ceil(R) - 1, ceil(R)] = [-halo, halo - 1], which with the corner n + 1
-  // keeps every read inside the staged tile + halo region.  The rotated
-  // variant takes R as the largest Euclidean tap length (the norm of a convex
-  // blend is at most the largest node norm) and reads (cos, sin) normalised
-  // to unit length by rotation_kernel, so each rotated component is within
-  // R (1 + 2^-20): the same argument holds.
-  const int nx = __float_as_int(r.x) - 0x4B400000;
-  const int ny = __float_as_int(r.y) - 0x4B400000;
-  const int e = base + ny * RW + nx;
-  const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y);
-  const float2 wy1 = __fmul2_rn(w, fy), wy0 = __ffma2_rn(wy1, make_float2(-1.f, -1.f), w);
-  const float2 w11 = __fmul2_rn(wy1, fx), w10 = __ffma2_rn(w11, make_float2(-1.f, -1.f), wy1);
-  const float2 w01 = __fmul2_rn(wy0, fx), w00 = __ffma2_rn(w01, make_float2(-1.f, -1.f), wy0);
-  add_corner<CH>(st, e, w00, acc);
-  add_corner<CH>(st, e + 1, w01, acc);
-  add_corner<CH>(st, e + RW, w10, acc);
-  add_corner<CH>(st, e + RW + 1, w11, acc);
+  if (ROT)
+    d = __ffma2_rn(make_float2(d.x, d.x), rv, __fmul2_rn(make_float2(d.y, d.y), make_float2(-rv.y, rv.x)));
+  float2 f;
+  const float2 r = sv_split_floor(d, f);
+  const int e = sv_index(sv_biased(base, RW), RW, r.x, r.y);
+  const CornerW cw = corner_weights(w, make_float2(f.x, f.x), make_float2(f.y, f.y));
+  const float2 wc[4] = {cw.w00, cw.w01, cw.w10, cw.w11};
+  const int ec[4] = {e, e + 1, e + RW, e + RW + 1};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (CH == 4) {
+      const float4 v = reinterpret_cast<const float4 *>(px)[ec[c]];
+      acc.p0 = __ffma2_rn(wc[c], lo2(v), acc.p0);
+      acc.p1 = __ffma2_rn(wc[c], hi2(v), acc.p1);
+    } else {
+      const float *v = px + 3 * ec[c];
+      acc.p0.x = fmaf(wc[c].x, v[0], acc.p0.x);
+      acc.p1.x = fmaf(wc[c].x, v[1], acc.p1.x);
+      acc.p2.x = fmaf(wc[c].x, v[2], acc.p2.x);
+    }
+  }
 }
 
-// The thread's N vertically adjacent pixels and one tap, top to bottom.
-// Neighbouring pixels' sample points usually have the same integer offset
-// (the offsets vary slowly across pixels), and then a pixel's top corners
-// are the previous pixel's bottom corners: they are kept in registers
-// instead of being read from shared memory again.
-template <int DIMS, int CH, bool ROT, int N>
-__device__ __forceinline__ void sv_tap_column(const float4 &q00, const float4 &q10, const float4 &q01,
-                                              const float4 &q11, const CellPairs *cp,
-                                              const RotPairs *rp, const Staged &st, int base0,
-                                              int RW, Acc *acc) {
+// One tap for the thread's N vertically adjacent pixels (4 channels), with
+// the top-row reuse of sv_pair_column.
+template <int DIMS, bool ROT, int N>
+__device__ __forceinline__ void sv_tap_column4(const float4 &q00, const float4 &q10,
+                                               const float4 &q01, const float4 &q11,
+                                               const CellPairs *cp, const float2 *rv,
+                                               const float *px, int base0, int RW, Acc *acc) {
+  const float4 *pv = reinterpret_cast<const float4 *>(px);
+  const unsigned biased0 = sv_biased(base0, RW);
   int eprev = 0;
-  float2 prg0 = make_float2(0.f, 0.f), prg1 = prg0, pba0 = prg0, pba1 = prg0;
-  auto accum = [&](Acc &a, const float2 &wb, const float2 &rg, const float2 &ba) {
-    a.rg = __ffma2_rn(wb, rg, a.rg);
-    a.b = fmaf(wb.x, ba.x, a.b);
-    if (CH == 4) a.a = fmaf(wb.x, ba.y, a.a);
-  };
-  auto load_ba = [&](int e) -> float2 {
-    return CH == 4 ? st.ba[e] : make_float2(st.b[e], 0.f);
-  };
+  float4 bl = make_float4(0.f, 0.f, 0.f, 0.f), br = bl;
 #pragma unroll
   for (int p = 0; p < N; ++p) {
     const CellPairs &a = cp[p];
@@ -242,43 +367,41 @@ __device__ __forceinline__ void sv_tap_column(const float4 &q00, const float4 &q
       d = __ffma2_rn(a.a11, lo2(q11), d);
       w = __ffma2_rn(a.a11, hi2(q11), w);
     }
-    if (ROT) d = __ffma2_rn(make_float2(d.x, d.x), rp[p].c, __fmul2_rn(make_float2(d.y, d.y), rp[p].s));
-    // split and bounds as in sv_tap
-    const float magic = 12582912.0f;
-    const float2 r = __fadd2_rn(__fadd2_rn(d, make_float2(-0.5f, -0.5f)), make_float2(magic, magic));
-    const float2 f = __ffma2_rn(__fadd2_rn(r, make_float2(-magic, -magic)), make_float2(-1.f, -1.f), d);
-    const int nx = __float_as_int(r.x) - 0x4B400000;
-    const int ny = __float_as_int(r.y) - 0x4B400000;
-    const int e = base0 + p * RW + ny * RW + nx;
-    const float2 fx = make_float2(f.x, f.x), fy = make_float2(f.y, f.y);
-    const float2 wy1 = __fmul2_rn(w, fy), wy0 = __ffma2_rn(wy1, make_float2(-1.f, -1.f), w);
-    const float2 w11 = __fmul2_rn(wy1, fx), w10 = __ffma2_rn(w11, make_float2(-1.f, -1.f), wy1);
-    const float2 w01 = __fmul2_rn(wy0, fx), w00 = __ffma2_rn(w01, make_float2(-1.f, -1.f), wy0);
-    float2 t0, t1, tb0, tb1;
+    if (ROT)
+      d = __ffma2_rn(make_float2(d.x, d.x), rv[p],
+                     __fmul2_rn(make_float2(d.y, d.y), make_float2(-rv[p].y, rv[p].x)));
+    float2 f;
+    const float2 r = sv_split_floor(d, f);
+    const int e = sv_index(biased0 + (unsigned)(p * RW), RW, r.x, r.y);
+    const CornerW cw = corner_weights(w, make_float2(f.x, f.x), make_float2(f.y, f.y));
+    float4 tl, tr;
     if (p > 0 && e == eprev + RW) {
-      t0 = prg0; t1 = prg1; tb0 = pba0; tb1 = pba1;
+      tl = bl; tr = br;
     } else {
-      t0 = st.rg[e]; t1 = st.rg[e + 1]; tb0 = load_ba(e); tb1 = load_ba(e + 1);
+      tl = pv[e]; tr = pv[e + 1];
     }
-    prg0 = st.rg[e + RW]; prg1 = st.rg[e + RW + 1];
-    pba0 = load_ba(e + RW); pba1 = load_ba(e + RW + 1);
+    bl = pv[e + RW];
+    br = pv[e + RW + 1];
     eprev = e;
-    accum(acc[p], w00, t0, tb0);
-    accum(acc[p], w01, t1, tb1);
-    accum(acc[p], w10, prg0, pba0);
-    accum(acc[p], w11, prg1, pba1);
+    Acc &ac = acc[p];
+    ac.p0 = __ffma2_rn(cw.w00, lo2(tl), ac.p0);
+    ac.p1 = __ffma2_rn(cw.w00, hi2(tl), ac.p1);
+    ac.p0 = __ffma2_rn(cw.w01, lo2(tr), ac.p0);
+    ac.p1 = __ffma2_rn(cw.w01, hi2(tr), ac.p1);
+    ac.p0 = __ffma2_rn(cw.w10, lo2(bl), ac.p0);
+    ac.p1 = __ffma2_rn(cw.w10, hi2(bl), ac.p1);
+    ac.p0 = __ffma2_rn(cw.w11, lo2(br), ac.p0);
+    ac.p1 = __ffma2_rn(cw.w11, hi2(br), ac.p1);
   }
 }
 
 template <int DIMS, int SRC, int DST, int TAPS, int CH, int PIX, bool ROT>
-__global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : 3)
+__global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : (CH == 3 ? 2 : 3))
 sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   constexpr int kSvPix = PIX, kSvTileH = PIX * kSvWarps;
   extern __shared__ __align__(128) unsigned char sm_raw[];
   const int halo = P.halo, hx = P.halo_x, RW = P.region_w, RH = kSvTileH + 2 * halo, RN = RW * RH;
-  float2 *s_rg = reinterpret_cast<float2 *>(sm_raw);
-  float *s_b = reinterpret_cast<float *>(sm_raw + sv_plane_b_offset(RN));
-  float2 *s_ba = reinterpret_cast<float2 *>(sm_raw + sv_plane_b_offset(RN));
+  float *s_px = reinterpret_cast<float *>(sm_raw);
   unsigned long long *s_bar = reinterpret_cast<unsigned long long *>(
       sm_raw + sv_smem_bytes(RN, CH) - 16);
   // The node taps the block needs, copied into shared memory after the
@@ -288,9 +411,9 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   unsigned *s_range = reinterpret_cast<unsigned *>(s_bar + 1);  // lowest, highest node
   const int tx0 = blockIdx.x * kSvTileW, ty0 = blockIdx.y * kSvTileH;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // The tensor copies need a 128-byte aligned destination; a block whose
+  // The tensor copy needs a 128-byte aligned destination; a block whose
   // shared window is not (never seen) records an error and does nothing.
-  const bool tma = SRC == PIX_PLANAR && P.use_tma;
+  const bool tma = SRC == PIX_F32 && P.use_tma;
   if (tma && (smem_addr(sm_raw) & 127u) != 0) {
     if (threadIdx.x == 0) atomicExch(P.err, DISK_ERR_UNSUPPORTED);
     return;
@@ -300,19 +423,18 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
     s_range[1] = 0u;
   }
   if (tma && threadIdx.x == 0) {
-    // Both planes of the region [ty0 - halo, +RH) x [tx0 - hx, +RW) in one
-    // phase of the barrier.  x offsets: 2 (tx0 - hx) floats for the pair
-    // planes, tx0 - hx for a b plane; tx0 is a multiple of 32 and hx of 4,
-    // so both start on 16-byte boundaries as the copy requires.
+    // The region [ty0 - halo, +RH) x [tx0 - hx, +RW) in one copy: rows of
+    // C * RW floats = C * RW / 2 eight-byte elements starting at element
+    // C (tx0 - hx) / 2; tx0 is a multiple of 32 and hx of 4, so the start
+    // is on a 16-byte boundary as the copy requires.
     const unsigned bar = smem_addr(s_bar);
-    const unsigned bytes = (unsigned)RN * (CH == 4 ? 16u : 12u);
+    const unsigned bytes = (unsigned)RN * (unsigned)sv_stage_bytes(CH);
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes)
                  : "memory");
-    tma_load_2d(s_rg, &P.tm_a, 2 * (tx0 - hx), ty0 - halo, bar);
-    tma_load_2d(s_b, &P.tm_b, CH == 4 ? 2 * (tx0 - hx) : tx0 - hx, ty0 - halo, bar);
+    tma_load_2d(s_px, &P.tm, CH * (tx0 - hx) / 2, ty0 - halo, bar);
   }
 
   const int x = tx0 + lane, xc = min(x, P.W - 1);
@@ -337,6 +459,20 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   }
   const bool ranged = TAPS == kSvTapsShared && !whole;
   if (tma || ranged) __syncthreads();  // the copy's mbarrier and the range slots are initialised
+  // one staged pixel: C floats at s_px + C e
+  auto put = [&](int e, const float4 &v) {
+    if (CH == 4) {
+      reinterpret_cast<float4 *>(s_px)[e] = v;
+    } else {
+      s_px[3 * e] = v.x;
+      s_px[3 * e + 1] = v.y;
+      s_px[3 * e + 2] = v.z;
+    }
+  };
+  auto get = [&](int e) -> float4 {
+    if (CH == 4) return reinterpret_cast<const float4 *>(s_px)[e];
+    return make_float4(s_px[3 * e], s_px[3 * e + 1], s_px[3 * e + 2], 0.f);
+  };
   if (tma) {
     const bool landed = mbar_wait(smem_addr(s_bar), 0);
     if (!__syncthreads_and(landed)) {
@@ -346,28 +482,21 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
       return;
     }
     // Clamp-to-edge for the parts of the region outside the image, which
-    // the copy filled with zeros: rows first (whole rows from the nearest
-    // image row, itself inside the region), then columns within each row.
+    // the copy filled with zeros (or, right of the last column, with the
+    // row's padding): rows first (whole rows from the nearest image row,
+    // itself inside the region), then columns within each row.
     const int y0 = ty0 - halo, x0 = tx0 - hx;
     if (y0 < 0 || y0 + RH > P.H || x0 < 0 || x0 + RW > P.W) {
       for (int e = threadIdx.x; e < RN; e += kSvThreads) {
         const int ry = e / RW, rx = e - ry * RW;
         const int gy = y0 + ry, cy = min(max(gy, 0), P.H - 1);
-        if (gy != cy) {
-          const int f = (cy - y0) * RW + rx;
-          s_rg[e] = s_rg[f];
-          if (CH == 4) s_ba[e] = s_ba[f]; else s_b[e] = s_b[f];
-        }
+        if (gy != cy) put(e, get((cy - y0) * RW + rx));
       }
       __syncthreads();
       for (int e = threadIdx.x; e < RN; e += kSvThreads) {
         const int ry = e / RW, rx = e - ry * RW;
         const int gx = x0 + rx, cx = min(max(gx, 0), P.W - 1);
-        if (gx != cx) {
-          const int f = ry * RW + (cx - x0);
-          s_rg[e] = s_rg[f];
-          if (CH == 4) s_ba[e] = s_ba[f]; else s_b[e] = s_b[f];
-        }
+        if (gx != cx) put(e, get(ry * RW + (cx - x0)));
       }
     }
   } else {
@@ -384,29 +513,18 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
         for (int u = 0; u < kStageRows; ++u) {
           const int ry = ry0 + u * kSvWarps;
           const int gy = min(max(ty0 - halo + ry, 0), P.H - 1);
-          if (ry < RH) {
-            if (SRC == PIX_PLANAR)
-              v[u] = load_planar(P.src, P.src_pitch, P.src_plane_b, CH, gy, gx);
-            else
-              v[u] = load_px<SRC == PIX_PLANAR ? PIX_F32 : SRC>(P.src, P.src_pitch, P.C, gy, gx);
-          }
+          if (ry < RH) v[u] = load_px<SRC>(P.src, P.src_pitch, P.C, gy, gx);
         }
 #pragma unroll
         for (int u = 0; u < kStageRows; ++u) {
           const int ry = ry0 + u * kSvWarps;
-          if (ry < RH) {
-            const int e = ry * RW + rx;
-            s_rg[e] = make_float2(v[u].x, v[u].y);
-            if (CH == 4) s_ba[e] = make_float2(v[u].z, v[u].w);
-            else s_b[e] = v[u].z;
-          }
+          if (ry < RH) put(ry * RW + rx, v[u]);
         }
       }
     }
   }
   Cell c[kSvPix];
   CellPairs cp[kSvPix];
-  RotPairs rp[kSvPix];
   int base[kSvPix];
   Acc acc[kSvPix];
   bool same = true;
@@ -414,9 +532,8 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   for (int j = 0; j < kSvPix; ++j) {
     c[j] = make_cell_v<DIMS>(P.ax, pv0[j], pv1[j]);
     cp[j] = cell_pairs(c[j]);
-    rp[j] = {rv[j], make_float2(-rv[j].y, rv[j].x)};
     base[j] = (warp * kSvPix + j + halo) * RW + (lane + hx);
-    acc[j] = {make_float2(0.f, 0.f), 0.f, 0.f};
+    acc[j] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     same = same && (c[j].n00 == c[0].n00);
   }
   // Node range of the block (lowest n00, highest n11 over its pixels); when
@@ -448,53 +565,88 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
     }
   }
   __syncthreads();
-  const Staged st{s_rg, s_b, s_ba};
+  const float *px = s_px;
 
   // The tap loops, once per source of node taps (the choice is uniform over
-  // the block).
-  auto run_taps = [&](auto fetch) {
+  // the block).  fetch(i): slot i of the table as a float4; fetch_w(i): its
+  // first two floats (the weight pair of the pair layout).
+  auto run_taps = [&](auto fetch, auto fetch_w) {
+    const int TP = CH == 3 ? (T & ~1) : 0;  // taps taken in pairs
+    // the taps of one pixel group (one cell) from node slot bases b[4]
+    auto pairs = [&](const int (&b)[4], auto column) {
+#pragma unroll 1
+      for (int i = 0; i < TP; i += 2) {
+        float4 A[4];
+        float2 Wt[4];
+        A[0] = fetch(b[0] + i);
+        A[1] = fetch(b[1] + i);
+        Wt[0] = fetch_w(b[0] + i + 1);
+        Wt[1] = fetch_w(b[1] + i + 1);
+        if (DIMS == 2) {
+          A[2] = fetch(b[2] + i);
+          A[3] = fetch(b[3] + i);
+          Wt[2] = fetch_w(b[2] + i + 1);
+          Wt[3] = fetch_w(b[3] + i + 1);
+        } else {
+          A[2] = A[0]; A[3] = A[1]; Wt[2] = Wt[0]; Wt[3] = Wt[1];
+        }
+        column(A, Wt);
+      }
+    };
     if (__all_sync(0xffffffffu, same)) {
       // each thread's pixels share a cell: one node fetch per tap serves them
-      const int b00 = c[0].n00 * T, b10 = c[0].n10 * T, b01 = c[0].n01 * T, b11 = c[0].n11 * T;
+      const int b[4] = {c[0].n00 * T, c[0].n10 * T, c[0].n01 * T, c[0].n11 * T};
+      if (CH == 3) {
+        pairs(b, [&](const float4 (&A)[4], const float2 (&Wt)[4]) {
+          sv_pair_column<DIMS, ROT, kSvPix>(A, Wt, cp, rv, px, base[0], RW, acc);
+        });
+      }
 #pragma unroll 2
-      for (int i = 0; i < T; ++i) {
-        const float4 q00 = fetch(b00 + i), q10 = fetch(b10 + i);
-        const float4 q01 = DIMS == 2 ? fetch(b01 + i) : q00;
-        const float4 q11 = DIMS == 2 ? fetch(b11 + i) : q10;
-        sv_tap_column<DIMS, CH, ROT, kSvPix>(q00, q10, q01, q11, cp, rp, st, base[0], RW, acc);
+      for (int i = TP; i < T; ++i) {
+        const float4 q00 = fetch(b[0] + i), q10 = fetch(b[1] + i);
+        const float4 q01 = DIMS == 2 ? fetch(b[2] + i) : q00;
+        const float4 q11 = DIMS == 2 ? fetch(b[3] + i) : q10;
+        if (CH == 4) {
+          sv_tap_column4<DIMS, ROT, kSvPix>(q00, q10, q01, q11, cp, rv, px, base[0], RW, acc);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kSvPix; ++j)
+            sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rv[j], px, base[j], RW, acc[j]);
+        }
       }
     } else {
       // unrolled so the per-pixel arrays stay in registers
 #pragma unroll
       for (int j = 0; j < kSvPix; ++j) {
-        const int b00 = c[j].n00 * T, b10 = c[j].n10 * T, b01 = c[j].n01 * T, b11 = c[j].n11 * T;
+        const int b[4] = {c[j].n00 * T, c[j].n10 * T, c[j].n01 * T, c[j].n11 * T};
+        if (CH == 3) {
+          pairs(b, [&](const float4 (&A)[4], const float2 (&Wt)[4]) {
+            sv_pair_column<DIMS, ROT, 1>(A, Wt, &cp[j], &rv[j], px, base[j], RW, &acc[j]);
+          });
+        }
 #pragma unroll 1
-        for (int i = 0; i < T; ++i) {
-          const float4 q00 = fetch(b00 + i), q10 = fetch(b10 + i);
-          const float4 q01 = DIMS == 2 ? fetch(b01 + i) : q00;
-          const float4 q11 = DIMS == 2 ? fetch(b11 + i) : q10;
-          sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rp[j], st, base[j], RW, acc[j]);
+        for (int i = TP; i < T; ++i) {
+          const float4 q00 = fetch(b[0] + i), q10 = fetch(b[1] + i);
+          const float4 q01 = DIMS == 2 ? fetch(b[2] + i) : q00;
+          const float4 q11 = DIMS == 2 ? fetch(b[3] + i) : q10;
+          sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rv[j], px, base[j], RW, acc[j]);
         }
       }
     }
   };
   if (TAPS == kSvTapsShared && shared_taps) {
     const float4 *t = s_taps - tap_base;
-    run_taps([&](int idx) { return t[idx]; });
+    run_taps([&](int idx) { return t[idx]; },
+             [&](int idx) { return *reinterpret_cast<const float2 *>(t + idx); });
   } else {
-    run_taps([&](int idx) { return __ldg(P.gtaps + idx); });
+    run_taps([&](int idx) { return __ldg(P.gtaps + idx); },
+             [&](int idx) { return __ldg(reinterpret_cast<const float2 *>(P.gtaps + idx)); });
   }
   if (x < P.W) {
 #pragma unroll
     for (int j = 0; j < kSvPix; ++j) {
       const int y = ty0 + warp * kSvPix + j;
-      if (y < P.H) {
-        const float4 v = make_float4(acc[j].rg.x, acc[j].rg.y, acc[j].b, acc[j].a);
-        if (DST == PIX_PLANAR)
-          store_planar(P.dst, P.dst_pitch, P.dst_plane_b, CH, y, x, v);
-        else
-          store_px<DST == PIX_PLANAR ? PIX_F32 : DST>(P.dst, P.dst_pitch, P.C, y, x, v);
-      }
+      if (y < P.H) store_px<DST>(P.dst, P.dst_pitch, P.C, y, x, acc_value<CH>(acc[j]));
     }
   }
 }
@@ -555,7 +707,10 @@ int launch_layer(int dims, bool shared_taps, bool rot, int src, int dst, int C,
               : launch_sv_layer_t<DIMS, S, D, TAPS, 3, 2, ROT>(P, s);                       \
   }
 
-// FP32 images: FP32 planes; FP16 images: FP16 planes (see intermediate_kind).
+// Storage combinations: the caller's FP32 or FP16 image in, FP32
+// intermediates between layers (sv_filter), FP32 / FP16 RGBA intermediates
+// (image adjoint's recomputation, no-allocation filter), the caller's
+// image out.
 #define DISK_SV_INSTANTIATE(DIMS, TAPS, ROT)                                                \
   template <>                                                                               \
   int launch_sv_layer<DIMS, TAPS, ROT>(int src, int dst, int C, const SvLayerParams &P,       \
@@ -569,11 +724,8 @@ int launch_layer(int dims, bool shared_taps, bool rot, int src, int dst, int C,
     DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA16, PIX_RGBA16)                                     \
     DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA16, PIX_F16)                                        \
     DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_F16)                                           \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F32, PIX_PLANAR)                                        \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_PLANAR)                                        \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_PLANAR, PIX_PLANAR)                                     \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_PLANAR, PIX_F32)                                        \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_PLANAR, PIX_F16)                                        \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_F32)                                           \
+    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F32, PIX_F16)                                           \
     return fail(DISK_ERR_INVALID_ARG, "unsupported layer storage combination");            \
   }
 
