@@ -41,7 +41,7 @@ OPS_PER_PX_TAP = 36
 SMS, FP32_LANES_PER_SM = 152, 128
 # DRAM bytes (read + write) of one pass (the L = 4 sv_layer launches) of the
 # current kernel, from an ncu capture of it; None whenever the kernel changes.
-TRAFFIC_PER_PASS = 847.2e6
+TRAFFIC_PER_PASS = 844.2e6
 
 
 def parse():
@@ -216,9 +216,16 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
                 "frac": achieved_gbs / (hbm or 6800.0),
                 "peak_source": "measured" if hbm else "fallback",
                 "bytes_per_px": BYTES_PER_PX}}
-    # shared-memory bound model: every tap reads four 16-byte corners
-    smem_bytes = px * taps * 4 * 16
-    out["smem_model"] = {"bytes_per_pass": smem_bytes, "achieved_gbs": smem_bytes / (ms * 1e-3) / 1e9}
+    # shared-memory model: every tap reads four corners of 3 FP32 channels
+    # from the staged region (the kernel reuses a pixel's bottom corners as
+    # the next pixel's top corners when they coincide, so it reads fewer);
+    # peak: 128 bytes per clock per SM
+    smem_bytes = px * taps * 4 * 12
+    smem_gbs = smem_bytes / (ms * 1e-3) / 1e9
+    smem_peak = SMS * 128 * sm_mhz * 1e6 / 1e9
+    out["smem_model"] = {"bytes_per_pass": smem_bytes, "achieved_gbs": smem_gbs,
+                         "peak_gbs": smem_peak, "frac": smem_gbs / smem_peak,
+                         "peak_source": f"derived: {SMS} SMs x 128 B x {sm_mhz:.0f} MHz"}
 
     # end to end through the public API with host buffers: the frame pipeline
     # copies every frame's image and maps in and its result out, the copies of
