@@ -119,10 +119,10 @@ void disk_basis_free(disk_basis *basis);
  *   not overlap.
  * d_maps: float [dims][H][W], dense, raw parameter values.
  * Limits: 1 <= H, W <= 32768; C in {3, 4}.
- * Intermediate layers are stored in FP32 whatever the image precision, as
- *   planes: (r, g) pairs and b (or (b, a) pairs), rows padded to a multiple
- *   of 4 pixels; arithmetic and accumulation are FP32.  The output is
- *   rounded to the image's precision (FP16 round to nearest even).
+ * Intermediate layers are stored in FP32 whatever the image precision, C
+ *   floats per pixel, rows padded to 16 bytes; arithmetic and accumulation
+ *   are FP32.  The output is rounded to the image's precision (FP16 round to
+ *   nearest even).
  * Scratch: two intermediate buffers (one for L = 2, none for L = 1) of
  *   about H * W * (C == 4 ? 16 : 12) bytes, plus, for the rotated variant,
  *   an H * W * 8-byte (cos, sin) plane, from the library's memory pool,

@@ -63,20 +63,24 @@ __global__ void wait_selftest_kernel(int *err, long long iters) {
 namespace {
 
 // Staging geometry of layer l: halo rows above and below the tile, halo_x
-// columns left and right.  Layers after the first read an FP32
-// intermediate, which the tensor-memory accelerator copies when the copy's
-// box fits its 256-element limit (rows of C (32 + 2 halo_x) floats, copied
-// as 8-byte elements: C (32 + 2 halo_x) / 2 <= 256); their halo_x is rounded
-// up to a multiple of 4 pixels so that every copy starts on a 16-byte
-// boundary (tile origins are multiples of 32).
+// columns left and right.  halo_x is the halo rounded up to a multiple of 16
+// pixels, which makes the staged row length 32 + 2 halo_x a multiple of 32
+// pixels: a warp whose lanes' integer offsets straddle two rows then reads
+// them without shared-memory bank conflicts (pixel k of row r + 1 lies in
+// the bank of pixel k of row r, and the lanes read distinct columns), and
+// every tensor copy starts on a 16-byte boundary (tile origins are
+// multiples of 32).  Layers after the first read an FP32 intermediate, which
+// the tensor-memory accelerator copies when the copy's box fits its
+// 256-element limit (rows of C (32 + 2 halo_x) floats, copied as 8-byte
+// elements: C (32 + 2 halo_x) / 2 <= 256).
 struct LayerGeom {
   int halo, halo_x, tma;
 };
 
 LayerGeom layer_geom(const disk_basis *b, int C, int l, bool rot) {
   const int h = halo_of(layer_reach(b, l, rot));
-  if (l == 0) return {h, h, 0};
-  const int hx = (h + 3) & ~3;
+  const int hx = (h + 15) & ~15;
+  if (l == 0) return {h, hx, 0};
   if (C * (kSvTileW + 2 * hx) / 2 <= 256) return {h, hx, 1};
   return {h, h, 0};
 }
