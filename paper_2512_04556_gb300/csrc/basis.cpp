@@ -1,5 +1,6 @@
 // Basis handles (Sec. 4.3, Eq. 8): construction, validation, file I/O,
 // error strings.  Host code only.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -182,18 +183,25 @@ extern "C" int disk_basis_from_arrays(int dims, const int *n_nodes, const float 
   // the device status word the filter kernels report to, allocated now so
   // that no later call (possibly inside a graph capture) has to
   if (!disk::device_error_word()) return fail(DISK_ERR_CUDA, "device status word allocation failed");
-  // the pair layout of the 3-channel filter, after the plain table
+  // the pair layout of the 3-channel filter, after the plain table: per node
+  // and tap pair (2j, 2j + 1), the offsets, then the weights of the node and
+  // of its successor on axis 0 (the cell corner n10 of a corner n00)
   const size_t nt = taps.size();
   taps.resize(2 * nt);
-  for (size_t r = 0; r < (size_t)L * b->B; ++r) {
-    const float4 *q = &taps[r * T];
-    float4 *o = &taps[nt + r * T];
-    for (int i = 0; i + 1 < T; i += 2) {
-      o[i] = make_float4(q[i].x, q[i + 1].x, q[i].y, q[i + 1].y);
-      o[i + 1] = make_float4(q[i].z, q[i + 1].z, q[i].z, q[i + 1].z);
+  const int n1 = dims == 2 ? n_nodes[1] : 1;
+  for (int l = 0; l < L; ++l)
+    for (int k = 0; k < b->B; ++k) {
+      const int k0 = k / n1, k1 = k % n1;
+      const int succ = std::min(k0 + 1, n_nodes[0] - 1) * n1 + k1;
+      const float4 *q = &taps[((size_t)l * b->B + k) * T];
+      const float4 *qs = &taps[((size_t)l * b->B + succ) * T];
+      float4 *o = &taps[nt + ((size_t)l * b->B + k) * T];
+      for (int i = 0; i + 1 < T; i += 2) {
+        o[i] = make_float4(q[i].x, q[i + 1].x, q[i].y, q[i + 1].y);
+        o[i + 1] = make_float4(q[i].z, q[i + 1].z, qs[i].z, qs[i + 1].z);
+      }
+      if (T & 1) o[T - 1] = q[T - 1];
     }
-    if (T & 1) o[T - 1] = q[T - 1];
-  }
   DISK_TRY_CUDA(cudaMalloc(&b->d_taps, taps.size() * sizeof(float4)), "cudaMalloc(basis)");
   b->d_taps_pair = b->d_taps + nt;
   cudaError_t e = cudaMemcpy(b->d_taps, taps.data(), taps.size() * sizeof(float4),

@@ -207,10 +207,12 @@ __device__ __forceinline__ float2 corners_into(float2 v, const CornerW &cw, cons
   return __ffma2_rn(cw.w11, br, v);
 }
 
-// Offsets of the pair layout of a node's T taps (3-channel images): for
-// each j < T / 2, slot 2j holds (dx_2j, dx_2j+1, dy_2j, dy_2j+1) and slot
-// 2j + 1 holds (w_2j, w_2j+1, w_2j, w_2j+1); an odd T's last slot holds its
-// last tap as (dx, dy, w, w).
+// The pair layout of a node's T taps (3-channel images): for each
+// j < T / 2, slot 2j holds (dx_2j, dx_2j+1, dy_2j, dy_2j+1) and slot 2j + 1
+// holds (w_2j, w_2j+1) of the node and then of its successor on axis 0
+// (node index + n1, or the node itself on the last row), so that one 16-byte
+// fetch from a cell's n00 (n01) gives the weights of n00 and n10 (n01 and
+// n11); an odd T's last slot holds its last tap as (dx, dy, w, w).
 
 // Eq. 9 blend of a tap pair's (dx, dy, w) for one pixel: lane 0 tap 2j,
 // lane 1 tap 2j + 1.
@@ -568,9 +570,8 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   const float *px = s_px;
 
   // The tap loops, once per source of node taps (the choice is uniform over
-  // the block).  fetch(i): slot i of the table as a float4; fetch_w(i): its
-  // first two floats (the weight pair of the pair layout).
-  auto run_taps = [&](auto fetch, auto fetch_w) {
+  // the block).  fetch(i): slot i of the table as a float4.
+  auto run_taps = [&](auto fetch) {
     const int TP = CH == 3 ? (T & ~1) : 0;  // taps taken in pairs
     // the taps of one pixel group (one cell) from node slot bases b[4]
     auto pairs = [&](const int (&b)[4], auto column) {
@@ -580,13 +581,17 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
         float2 Wt[4];
         A[0] = fetch(b[0] + i);
         A[1] = fetch(b[1] + i);
-        Wt[0] = fetch_w(b[0] + i + 1);
-        Wt[1] = fetch_w(b[1] + i + 1);
+        // a weight slot holds the pair of its node and of the node next on
+        // axis 0: n10 of an n00, n11 of an n01
+        const float4 w0 = fetch(b[0] + i + 1);
+        Wt[0] = lo2(w0);
+        Wt[1] = hi2(w0);
         if (DIMS == 2) {
           A[2] = fetch(b[2] + i);
           A[3] = fetch(b[3] + i);
-          Wt[2] = fetch_w(b[2] + i + 1);
-          Wt[3] = fetch_w(b[3] + i + 1);
+          const float4 w1 = fetch(b[2] + i + 1);
+          Wt[2] = lo2(w1);
+          Wt[3] = hi2(w1);
         } else {
           A[2] = A[0]; A[3] = A[1]; Wt[2] = Wt[0]; Wt[3] = Wt[1];
         }
@@ -636,11 +641,9 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   };
   if (TAPS == kSvTapsShared && shared_taps) {
     const float4 *t = s_taps - tap_base;
-    run_taps([&](int idx) { return t[idx]; },
-             [&](int idx) { return *reinterpret_cast<const float2 *>(t + idx); });
+    run_taps([&](int idx) { return t[idx]; });
   } else {
-    run_taps([&](int idx) { return __ldg(P.gtaps + idx); },
-             [&](int idx) { return __ldg(reinterpret_cast<const float2 *>(P.gtaps + idx)); });
+    run_taps([&](int idx) { return __ldg(P.gtaps + idx); });
   }
   if (x < P.W) {
 #pragma unroll
