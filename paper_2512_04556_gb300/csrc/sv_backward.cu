@@ -32,9 +32,16 @@ struct BwParams {
   float4 *gdst;         // gradient of this layer's input: FP32 RGBA plane, pre-zeroed
   const float *maps;
   const float4 *taps;   // [B][T] of this layer: (dx, dy, w, w)
-  int H, W, C, T, halo, region_w;
+  int H, W, C, T, halo;
+  int halo_x;           // columns left and right of the tile: bw_halo_x(halo)
+  int region_w;         // kBwTileW + 2 halo_x
   AxisNodes ax[2];
 };
+
+// Column halo of the image adjoint's region: the halo rounded up to 16
+// pixels, so that region rows are a multiple of 32 floats and a warp whose
+// lanes' corners straddle two rows adds to distinct banks.
+inline int bw_halo_x(int halo) { return (halo + 15) & ~15; }
 
 template <int DIMS, int GKIND, int CH>
 __global__ void __launch_bounds__(kBwThreads)
@@ -44,7 +51,7 @@ sv_adjoint_layer_kernel(const __grid_constant__ BwParams P) {
   extern __shared__ float acc[];
   const int halo = P.halo, RW = P.region_w, RH = kBwTileH + 2 * halo, RN = RW * RH;
   const int tx0 = blockIdx.x * kBwTileW, ty0 = blockIdx.y * kBwTileH;
-  const int ox = tx0 - halo, oy = ty0 - halo;  // image coordinates of region (0, 0)
+  const int ox = tx0 - P.halo_x, oy = ty0 - halo;  // image coordinates of region (0, 0)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = threadIdx.x; j < RN * CH; j += kBwThreads) acc[j] = 0.f;
   __syncthreads();
@@ -467,7 +474,7 @@ extern "C" int disk_sv_filter_backward_image(const disk_basis *b, const void *d_
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
   for (int l = 0; l < b->L; ++l) {
     const int h = halo_of(b->reach[l]);
-    if ((size_t)(kBwTileW + 2 * h) * (kBwTileH + 2 * h) * sizeof(float4) > (size_t)kBwMaxSmem)
+    if ((size_t)(kBwTileW + 2 * bw_halo_x(h)) * (kBwTileH + 2 * h) * sizeof(float4) > (size_t)kBwMaxSmem)
       return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -494,7 +501,8 @@ extern "C" int disk_sv_filter_backward_image(const disk_basis *b, const void *d_
     e = cudaMemsetAsync(dst, 0, plane, s);
     if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync(backward plane)"); break; }
     P.halo = halo_of(b->reach[l]);
-    P.region_w = kBwTileW + 2 * P.halo;
+    P.halo_x = bw_halo_x(P.halo);
+    P.region_w = kBwTileW + 2 * P.halo_x;
     P.taps = b->d_taps + (size_t)l * b->B * b->T;
     P.gdst = dst;
     const int gkind = l == b->L - 1 ? user : PIX_RGBA32;
@@ -533,7 +541,7 @@ extern "C" int disk_sv_filter_backward(const disk_basis *b, const void *d_in, si
   for (int l = 0; l < b->L; ++l) {
     const int h = halo_of(b->reach[l]);
     const size_t region = (size_t)(kBwTileW + 2 * h) * (kBwTileH + 2 * h);
-    if (region * sizeof(float4) > (size_t)kBwMaxSmem ||
+    if ((size_t)(kBwTileW + 2 * bw_halo_x(h)) * (kBwTileH + 2 * h) * sizeof(float4) > (size_t)kBwMaxSmem ||
         ((region * stage_px + 15) & ~(size_t)15) + (size_t)b->B * b->T * 12 > (size_t)kBwMaxSmem)
       return fail(DISK_ERR_UNSUPPORTED, "layer halo or basis size exceeds shared memory");
   }
@@ -585,7 +593,7 @@ extern "C" int disk_sv_filter_backward(const disk_basis *b, const void *d_in, si
       e = cudaMemsetAsync(dst, 0, g_plane, s);
       if (e != cudaSuccess) { rc = cuda_fail(e, "cudaMemsetAsync(backward plane)"); break; }
       BP.gsrc = gptr; BP.gsrc_pitch = gpitch; BP.gdst = dst; BP.taps = ltaps;
-      BP.halo = halo; BP.region_w = kBwTileW + 2 * halo;
+      BP.halo = halo; BP.halo_x = bw_halo_x(halo); BP.region_w = kBwTileW + 2 * BP.halo_x;
       rc = b->dims == 1 ? dispatch_adjoint<1>(gkind, C, BP, s) : dispatch_adjoint<2>(gkind, C, BP, s);
       g_src = dst;
       k ^= 1;
