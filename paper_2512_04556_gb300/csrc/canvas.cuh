@@ -40,14 +40,41 @@ __device__ __forceinline__ int split_floor(float d, float &f) {
   return __float2int_rn(fl);
 }
 
-// One shift-invariant layer (Eq. 3) with the tap set taps[T] (dx, dy, w):
+// One shift-invariant layer's taps prepared for a sweep: per tap the offset
+// of its corner (0, 0) from the output pixel in canvas elements and the four
+// bilinear corner weights times w, (w00, w01, w10, w11) -- the taps are the
+// same at every pixel, so the split and the weights are taken once per layer.
+struct PreparedTaps {
+  float4 w[DISK_MAX_TAPS];
+  int off[DISK_MAX_TAPS];
+};
+
+// Fills p from taps[T] (dx, dy, w) for a canvas of half-width R; sign = -1
+// applies the taps at -o (the adjoint of a layer on a zero-bounded canvas,
+// by the symmetry of the bilinear tent).  halo bounds every tap's reach as
+// ceil(reach) + 1.  Run by the threads of one CTA; the caller synchronises
+// the CTA before a sweep reads p.
+__device__ __forceinline__ void prepare_taps(PreparedTaps &p, const float4 *taps, int T, int halo,
+                                             float sign, int R) {
+  const int N = 2 * R + 1;
+  for (int i = threadIdx.x; i < T; i += blockDim.x) {
+    const float4 t = taps[i];
+    float fx, fy;
+    const int nx = min(max(split_floor(sign * t.x, fx), -halo), halo - 1);
+    const int ny = min(max(split_floor(sign * t.y, fy), -halo), halo - 1);
+    const float wy1 = t.z * fy, wy0 = t.z - wy1;
+    const float w11 = wy1 * fx, w10 = wy1 - w11, w01 = wy0 * fx, w00 = wy0 - w01;
+    p.w[i] = make_float4(w00, w01, w10, w11);
+    p.off[i] = ny * N + nx;
+  }
+}
+
+// One shift-invariant layer (Eq. 3) with prepared taps p[T]:
 // dst[p] = sum_i w_i * bilinear(src, p + o_i) for every p with
 // max(|p - c|) <= b.  src must hold the true values (zeros outside the
-// support) on the box of half-width b + halo; halo bounds every tap's reach
-// as ceil(reach) + 1.  sign = -1 applies the taps at -o (the adjoint of a
-// layer on a zero-bounded canvas, by the symmetry of the bilinear tent).
+// support) on the box of half-width b + halo.
 __device__ __forceinline__ void canvas_layer(const float *src, float *dst, int R, int b,
-                                             const float4 *taps, int T, int halo, float sign,
+                                             const PreparedTaps &p, int T,
                                              int tid = threadIdx.x, int nthr = blockDim.x) {
   const int side = 2 * b + 1, N = 2 * R + 1;
   for (int j = tid; j < side * side; j += nthr) {
@@ -55,15 +82,9 @@ __device__ __forceinline__ void canvas_layer(const float *src, float *dst, int R
     const float *base = src + (R + v) * N + (R + u);
     float acc = 0.f;
     for (int i = 0; i < T; ++i) {
-      const float4 t = taps[i];
-      float fx, fy;
-      const int nx = min(max(split_floor(sign * t.x, fx), -halo), halo - 1);
-      const int ny = min(max(split_floor(sign * t.y, fy), -halo), halo - 1);
-      const float *q = base + ny * N + nx;
-      const float c00 = q[0], c01 = q[1], c10 = q[N], c11 = q[N + 1];
-      const float wy1 = t.z * fy, wy0 = t.z - wy1;
-      const float w11 = wy1 * fx, w10 = wy1 - w11, w01 = wy0 * fx, w00 = wy0 - w01;
-      acc += w00 * c00 + w01 * c01 + w10 * c10 + w11 * c11;
+      const float4 w = p.w[i];
+      const float *q = base + p.off[i];
+      acc += w.x * q[0] + w.y * q[1] + w.z * q[N] + w.w * q[N + 1];
     }
     dst[(R + v) * N + (R + u)] = acc;
   }

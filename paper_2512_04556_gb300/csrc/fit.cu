@@ -240,6 +240,7 @@ struct FitShared {
   float vo[kFitMaxTaps * 3];
   float g[kFitMaxTaps * 3];
   LayerExtent ext[DISK_MAX_LAYERS];
+  PreparedTaps pt;  // the layer being swept
   float red[kFitMaxWarps];
   float closs;  // this CTA's share of the loss
   // per-(chunk, tap) partial tap gradients of the warps of this CTA
@@ -312,7 +313,9 @@ __device__ float forward_loss(FitShared &sh, const FitArgs &A, const FitMeta &m,
   target_sync<CL>();
   for (int l = 0; l < L; ++l) {
     const int S = sh.ext[l].S;
-    canvas_layer(act[l], act[l + 1], R, S, sh.taps + l * T, T, sh.ext[l].H, 1.f, tid, nthr);
+    prepare_taps(sh.pt, sh.taps + l * T, T, sh.ext[l].H, 1.f, R);
+    __syncthreads();
+    canvas_layer(act[l], act[l + 1], R, S, sh.pt, T, tid, nthr);
     const int reach = (l + 1 < L) ? S + 2 * sh.ext[l + 1].H : max(S, h);
     zero_frame(act[l + 1], R, S, reach, tid, nthr);  // disjoint from the layer's box
     target_sync<CL>();
@@ -402,7 +405,9 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     }
     if (l > 0) {
       // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
-      canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.taps + l * T, T, halo, -1.f, tid, nthr);
+      prepare_taps(sh.pt, sh.taps + l * T, T, halo, -1.f, R);
+      __syncthreads();
+      canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.pt, T, tid, nthr);
     }
     target_sync<CL>();  // the adjoint plane is whole; every CTA has read the partial sums
     float *t = G; G = Gn; Gn = t;

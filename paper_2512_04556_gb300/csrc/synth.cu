@@ -21,6 +21,7 @@ synth_kernel(const float *theta, int L, int T, int K, float max_reach, int R, fl
              float *out) {
   extern __shared__ float4 taps[];  // [L][T]
   __shared__ LayerExtent ext[DISK_MAX_LAYERS];
+  __shared__ PreparedTaps pt;
   __shared__ int bad;
   const int b = blockIdx.x, N = 2 * R + 1, hw = (K - 1) / 2;
   const float *th = theta + (size_t)b * L * T * 3;
@@ -66,7 +67,9 @@ synth_kernel(const float *theta, int L, int T, int K, float max_reach, int R, fl
   if (threadIdx.x == 0) pa[R * N + R] = 1.f;
   __syncthreads();
   for (int l = 0; l < L; ++l) {
-    canvas_layer(pa, pb, R, bl[l], taps + l * T, T, ext[l].H, 1.f);
+    prepare_taps(pt, taps + l * T, T, ext[l].H, 1.f, R);
+    __syncthreads();
+    canvas_layer(pa, pb, R, bl[l], pt, T);
     __syncthreads();
     if (l + 1 < L) {
       zero_frame(pb, R, bl[l], bl[l + 1] + ext[l + 1].H);
