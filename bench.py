@@ -41,7 +41,7 @@ OPS_PER_PX_TAP = 36
 SMS, FP32_LANES_PER_SM = 152, 128
 # DRAM bytes (read + write) of one pass (the L = 4 sv_layer launches) of the
 # current kernel, from an ncu capture of it; None whenever the kernel changes.
-TRAFFIC_PER_PASS = 845.8e6
+TRAFFIC_PER_PASS = 845.5e6
 
 
 def parse():

@@ -98,6 +98,25 @@ def test_2d_basis(torch_cuda, dtype):
     check(torch_cuda, img, _maps(45, 77, 1.0, 9.0, 8, dims=2), axes, th)
 
 
+@pytest.mark.parametrize("C", [3, 4])
+@pytest.mark.parametrize("smooth", [True, False])
+def test_2d_large_table_odd_taps(torch_cuda, C, smooth):
+    """A 10 x 10 basis with T = 7 (the node-tap table exceeds 8 KB, so blocks
+    copy only their node range, or read the table from global memory when the
+    range is too wide): taps taken in pairs plus the odd last tap for three
+    channels, one at a time for four; smooth maps (one cell per thread) and
+    per-pixel noise on the second axis (cells differ within threads)."""
+    n0 = n1 = 10
+    axes = [list(np.linspace(2.0, 8.0, n0)), list(np.linspace(0.0, 1.0, n1))]
+    th = wl.basis_random(np.repeat(np.linspace(0.5, 1.5, n0), n1), 2, 7, 2.0, seed=81)
+    H, W = 70, 90
+    img = wl.image_uniform(H, W, C, seed=82)
+    m0 = wl.param_map(H, W, 1.0, 9.0, 8.0, 83)
+    m1 = (wl.param_map(H, W, 0.0, 1.0, 8.0, 84) if smooth
+          else np.random.default_rng(85).uniform(0, 1, (H, W)).astype(np.float32))
+    check(torch_cuda, img, np.stack([m0, m1]), axes, th)
+
+
 def test_edge_offsets_integer_and_half(torch_cuda):
     """Exact integer and +-1/2 offsets (the floor/fraction split's edge cases)."""
     th = np.zeros((2, 2, 4, 3), np.float32)
