@@ -69,8 +69,10 @@ namespace {
 // them without shared-memory bank conflicts (pixel k of row r + 1 lies in
 // the bank of pixel k of row r, and the lanes read distinct columns), and
 // every tensor copy starts on a 16-byte boundary (tile origins are
-// multiples of 32).  Layers after the first read an FP32 intermediate, which
-// the tensor-memory accelerator copies when the copy's box fits its
+// multiples of 32).  Where that region would not fit shared memory the halo
+// is rounded up to 4 pixels only (tensor copies), or not at all (staging
+// through registers).  Layers after the first read an FP32 intermediate,
+// which the tensor-memory accelerator copies when the copy's box fits its
 // 256-element limit (rows of C (32 + 2 halo_x) floats, copied as 8-byte
 // elements: C (32 + 2 halo_x) / 2 <= 256).
 struct LayerGeom {
@@ -79,9 +81,14 @@ struct LayerGeom {
 
 LayerGeom layer_geom(const disk_basis *b, int C, int l, bool rot) {
   const int h = halo_of(layer_reach(b, l, rot));
-  const int hx = (h + 15) & ~15;
-  if (l == 0) return {h, hx, 0};
-  if (C * (kSvTileW + 2 * hx) / 2 <= 256) return {h, hx, 1};
+  // a column halo whose region (with the smallest tile) fits shared memory;
+  // the widest halos give up the rounding rather than the layer
+  const size_t rows = (size_t)sv_tile_h(kSvDefaultPix) + 2 * h;
+  auto fits = [&](int hx) { return sv_smem_bytes((kSvTileW + 2 * (size_t)hx) * rows, C) <= kSvMaxSmem; };
+  const int hx16 = (h + 15) & ~15, hx4 = (h + 3) & ~3;
+  if (l == 0) return {h, fits(hx16) ? hx16 : h, 0};
+  for (const int hx : {hx16, hx4})
+    if (C * (kSvTileW + 2 * hx) / 2 <= 256 && fits(hx)) return {h, hx, 1};
   return {h, h, 0};
 }
 

@@ -131,15 +131,19 @@ def test_rotated_halo_limit(torch_cuda):
     assert e.value.code == -3 or "halo" in str(e.value)
 
 
-def test_rotated_long_taps_stage_through_registers(torch_cuda):
-    """Taps up to 36 px on both axes (51 px long) give a rotated halo of 52 px:
-    the tile copy's box would exceed the tensor-memory accelerator's
-    256-element limit, so the intermediate layers stage their planar source
-    through registers."""
+@pytest.mark.parametrize("h0", [52, 56])
+def test_rotated_long_taps(torch_cuda, h0):
+    """Taps up to 36 px on both axes (51 px long) give a rotated halo of 52 px,
+    staged rows of 32 + 2 x 64 pixels (the tile copy's box: 240 eight-byte
+    elements of the 256 allowed) and a first-layer region at the edge of
+    shared memory; a diagonal tap of 38.2 px per axis (halo 56) leaves the
+    regions rounded to 16 pixels too large, so the first layer keeps its
+    exact halo and the others round it to 4 pixels only."""
     img, maps, axes, th, angle = _case(120, 140, 1, 3, 4, 1.0, 17)
     g = np.random.default_rng(5)
     th[..., :2] = g.uniform(-36.0, 36.0, th[..., :2].shape)
-    th[:, :, 0, 0], th[:, :, 0, 1] = 36.0, -36.0      # one diagonal tap per layer
+    d = 36.0 if h0 == 52 else 38.2
+    th[:, :, 0, 0], th[:, :, 0, 1] = d, -d            # one diagonal tap per layer
     got = _gpu(torch_cuda, img, maps, axes, th, angle)
     assert rel_err(got, _oracle(img, maps, axes, th, angle)) <= TOL32
 
