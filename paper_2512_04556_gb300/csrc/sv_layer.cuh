@@ -38,8 +38,10 @@
 namespace disk {
 
 // Tile configurations: 32 columns x (8 warps x PIX rows); PIX pixels per
-// thread.  PIX = 4 (32 x 32 tiles, 3 CTAs per SM) or PIX = 2 (32 x 16 tiles,
-// 4 CTAs per SM); disk_sv_filter_autotune picks per frame shape.
+// thread.  PIX = 2: 32 x 16 tiles, 4 CTAs per SM (64 registers); PIX = 4:
+// 32 x 32 tiles, 3 CTAs per SM for four channels and 2 for three (whose tap
+// pairs keep 128 registers busy); disk_sv_filter_autotune picks per layer
+// and frame shape.
 constexpr int kSvTileW = 32, kSvThreads = 256;
 constexpr int kSvWarps = kSvThreads / 32;
 constexpr int kSvDefaultPix = 2;
