@@ -81,6 +81,30 @@ def test_ragged_sizes(torch_cuda, H, W):
     check(torch_cuda, img, _maps(H, W, 0.5, 9.0, W), axes, th)
 
 
+@pytest.mark.parametrize("H,W,dtype", [(1, 32768, "f32"), (32768, 1, "f32"), (3, 32768, "f16"),
+                                        (32768, 2, "f16")])
+def test_maximum_image_sides(torch_cuda, H, W, dtype):
+    """Images at the 32768-pixel limit on either side (grid limits, index
+    arithmetic, the tile copy's tensor map) against the oracle."""
+    axes, th = _basis_1d(2, 5, 1.5, 91)
+    img = wl.image_uniform(H, W, 3, seed=92)
+    if dtype == "f16":
+        img = wl.to_fp16(img)
+    check(torch_cuda, img, _maps(H, W, 1.0, 8.0, 93), axes, th)
+
+
+def test_rejects_sides_beyond_limit(torch_cuda):
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    axes, th = _basis_1d(2, 3, 1.0, 94)
+    b = disk.Basis.from_arrays(axes, th)
+    t = torch.zeros((1, 32769, 3), device="cuda")
+    m = torch.zeros((1, 1, 32769), device="cuda")
+    with pytest.raises(disk.DiskError) as e:
+        disk.sv_filter(b, t, m)
+    assert e.value.code == -1
+
+
 def test_fp16_storage(torch_cuda):
     axes, th = _basis_1d(4, 8, 1.2, 3)
     img = wl.to_fp16(wl.image_rects(70, 91, seed=4))
