@@ -447,8 +447,7 @@ int recompute_activations(const disk_basis *b, const void *d_in, size_t in_pitch
     P.bt = b->B * b->T;
     const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(kSvDefaultPix) + 2 * P.halo), C);
     P.tap_cap = sv_tap_cap(b->dims, b->n_nodes[1], b->B, b->T, region);
-    const int rc = launch_layer(b->dims, P.tap_cap > 0, false, l == 0 ? user : mid, mid,
-                                C, P, s, kSvDefaultPix);
+    const int rc = launch_layer(b->dims, false, l == 0 ? user : mid, mid, C, P, s, kSvDefaultPix);
     if (rc) return rc;
   }
   return DISK_OK;

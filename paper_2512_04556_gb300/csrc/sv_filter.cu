@@ -30,16 +30,13 @@ __global__ void rotation_kernel(const float *__restrict__ angle, float2 *__restr
   }
 }
 
-int launch_layer(int dims, bool shared_taps, bool rot, int src, int dst, int C,
-                 const SvLayerParams &P, cudaStream_t s, int pix) {
-  // One instantiation serves both: with tap_cap == 0 its blocks read the
-  // taps from global memory.
-  (void)shared_taps;
+int launch_layer(int dims, bool rot, int src, int dst, int C, const SvLayerParams &P,
+                 cudaStream_t s, int pix) {
   if (dims == 1)
-    return rot ? launch_sv_layer<1, kSvTapsShared, true>(src, dst, C, P, s, pix)
-               : launch_sv_layer<1, kSvTapsShared, false>(src, dst, C, P, s, pix);
-  return rot ? launch_sv_layer<2, kSvTapsShared, true>(src, dst, C, P, s, pix)
-             : launch_sv_layer<2, kSvTapsShared, false>(src, dst, C, P, s, pix);
+    return rot ? launch_sv_layer<1, true>(src, dst, C, P, s, pix)
+               : launch_sv_layer<1, false>(src, dst, C, P, s, pix);
+  return rot ? launch_sv_layer<2, true>(src, dst, C, P, s, pix)
+             : launch_sv_layer<2, false>(src, dst, C, P, s, pix);
 }
 
 // Exercises the bounded wait of the tile copies: the block arms an
@@ -205,7 +202,7 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
     if (ev) cudaEventRecord(ev[l], s);
     const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(pix[l]) + 2 * P.halo), C);
     P.tap_cap = sv_tap_cap(b->dims, b->n_nodes[1], b->B, b->T, region);
-    rc = launch_layer(b->dims, P.tap_cap > 0, rotated, src, dst, C, P, s, pix[l]);
+    rc = launch_layer(b->dims, rotated, src, dst, C, P, s, pix[l]);
   }
   if (ev && rc == DISK_OK) cudaEventRecord(ev[L], s);
   for (int i = 0; i < nbuf; ++i) cudaFreeAsync(bufs[i], s);

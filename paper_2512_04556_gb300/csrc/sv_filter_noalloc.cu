@@ -69,7 +69,7 @@ int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
     P.bt = b->B * b->T;
     const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(kSvDefaultPix) + 2 * P.halo), C);
     P.tap_cap = sv_tap_cap(b->dims, b->n_nodes[1], b->B, b->T, region);
-    rc = launch_layer(b->dims, P.tap_cap > 0, false, src, dst, C, P, s, kSvDefaultPix);
+    rc = launch_layer(b->dims, false, src, dst, C, P, s, kSvDefaultPix);
   }
   return rc;
 }

@@ -46,10 +46,6 @@ constexpr int kSvTileW = 32, kSvThreads = 256;
 constexpr int kSvWarps = kSvThreads / 32;
 constexpr int kSvDefaultPix = 2;
 __host__ __device__ constexpr int sv_tile_h(int pix) { return pix * kSvWarps; }
-// Where a layer reads its node taps (B x T float4 (dx, dy, w, w)): a copy
-// each block makes in shared memory, or global memory through L1 when that
-// copy does not fit beside the staged region.
-enum : int { kSvTapsGlobal = 0, kSvTapsShared = 1 };
 constexpr int kSvMaxSmem = 232448;           // 227 KB opt-in shared memory per CTA
 
 // Shared-memory bytes per staged pixel: C FP32 values.
@@ -399,7 +395,7 @@ __device__ __forceinline__ void sv_tap_column4(const float4 &q00, const float4 &
   }
 }
 
-template <int DIMS, int SRC, int DST, int TAPS, int CH, int PIX, bool ROT>
+template <int DIMS, int SRC, int DST, int CH, int PIX, bool ROT>
 __global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : (CH == 3 ? 2 : 3))
 sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   constexpr int kSvPix = PIX, kSvTileH = PIX * kSvWarps;
@@ -422,7 +418,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
     if (threadIdx.x == 0) atomicExch(P.err, DISK_ERR_UNSUPPORTED);
     return;
   }
-  if (TAPS == kSvTapsShared && threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
     s_range[0] = 0xffffffffu;
     s_range[1] = 0u;
   }
@@ -446,7 +442,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   const int T = P.T;
   // A table small enough for every block to hold whole is copied now,
   // overlapping the tile copy; larger ones are copied per node range below.
-  const bool whole = TAPS == kSvTapsShared && P.tap_cap * T >= P.bt;
+  const bool whole = P.tap_cap * T >= P.bt;
   if (whole)
     for (int i = threadIdx.x; i < P.bt; i += kSvThreads) s_taps[i] = __ldg(P.gtaps + i);
   // This thread's map values (and rotations), loaded before the staging so
@@ -461,7 +457,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
     pv1[j] = DIMS == 2 ? __ldg(P.maps + HW + px) : 0.f;
     rv[j] = ROT ? __ldg(P.rot + px) : make_float2(1.f, 0.f);
   }
-  const bool ranged = TAPS == kSvTapsShared && !whole;
+  const bool ranged = !whole;
   if (tma || ranged) __syncthreads();  // the copy's mbarrier and the range slots are initialised
   // one staged pixel: C floats at s_px + C e
   auto put = [&](int e, const float4 &v) {
@@ -641,7 +637,7 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
       }
     }
   };
-  if (TAPS == kSvTapsShared && shared_taps) {
+  if (shared_taps) {
     const float4 *t = s_taps - tap_base;
     run_taps([&](int idx) { return t[idx]; });
   } else {
@@ -661,12 +657,12 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
 __global__ void rotation_kernel(const float *__restrict__ angle, float2 *__restrict__ rot,
                                 long long n);
 
-template <int DIMS, int SRC, int DST, int TAPS, int CH, int PIX, bool ROT>
+template <int DIMS, int SRC, int DST, int CH, int PIX, bool ROT>
 int launch_sv_layer_t(const SvLayerParams &P, cudaStream_t s) {
-  auto k = sv_layer_kernel<DIMS, SRC, DST, TAPS, CH, PIX, ROT>;
+  auto k = sv_layer_kernel<DIMS, SRC, DST, CH, PIX, ROT>;
   constexpr int kSvTileH = PIX * kSvWarps;
   const size_t smem = sv_smem_bytes((size_t)P.region_w * (kSvTileH + 2 * P.halo), CH) +
-                      (TAPS == kSvTapsShared ? (size_t)P.tap_cap * P.T * sizeof(float4) : 0);
+                      (size_t)P.tap_cap * P.T * sizeof(float4);
   static unsigned long long attr_set = 0;  // per instantiation, one bit per device
   int dev = 0;
   cudaGetDevice(&dev);
@@ -682,9 +678,9 @@ int launch_sv_layer_t(const SvLayerParams &P, cudaStream_t s) {
 }
 
 // Storage combination of one layer: (source kind, destination kind), tile
-// configuration pix (2 or 4 pixels per thread); TAPS where the node taps are
-// read; ROT selects the rotated variant (P.rot set).
-template <int DIMS, int TAPS, bool ROT>
+// configuration pix (2 or 4 pixels per thread); ROT selects the rotated
+// variant (P.rot set).
+template <int DIMS, bool ROT>
 int launch_sv_layer(int src, int dst, int C, const SvLayerParams &P, cudaStream_t s, int pix);
 
 // How many nodes' taps a block copies into shared memory (0: the layer reads
@@ -698,39 +694,40 @@ inline int sv_tap_cap(int dims, int n1, int B, int T, size_t region_smem) {
   return region_smem + (size_t)cap * T * sizeof(float4) <= (size_t)kSvMaxSmem ? cap : 0;
 }
 
-// One layer of any variant: dims 1 or 2, taps in shared memory or global
-// (defined with the filter's host code).
-int launch_layer(int dims, bool shared_taps, bool rot, int src, int dst, int C,
-                 const SvLayerParams &P, cudaStream_t s, int pix);
+// One layer of any variant: dims 1 or 2, rotated or not; the node taps come
+// from shared memory when P.tap_cap allows, else from global memory (defined
+// with the filter's host code).
+int launch_layer(int dims, bool rot, int src, int dst, int C, const SvLayerParams &P,
+                 cudaStream_t s, int pix);
 
-#define DISK_SV_CASE(DIMS, TAPS, ROT, S, D)                                                 \
+#define DISK_SV_CASE(DIMS, ROT, S, D)                                                       \
   if (src == S && dst == D) {                                                               \
     if (pix == 4)                                                                           \
-      return c4 ? launch_sv_layer_t<DIMS, S, D, TAPS, 4, 4, ROT>(P, s)                      \
-                : launch_sv_layer_t<DIMS, S, D, TAPS, 3, 4, ROT>(P, s);                     \
-    return c4 ? launch_sv_layer_t<DIMS, S, D, TAPS, 4, 2, ROT>(P, s)                        \
-              : launch_sv_layer_t<DIMS, S, D, TAPS, 3, 2, ROT>(P, s);                       \
+      return c4 ? launch_sv_layer_t<DIMS, S, D, 4, 4, ROT>(P, s)                            \
+                : launch_sv_layer_t<DIMS, S, D, 3, 4, ROT>(P, s);                           \
+    return c4 ? launch_sv_layer_t<DIMS, S, D, 4, 2, ROT>(P, s)                              \
+              : launch_sv_layer_t<DIMS, S, D, 3, 2, ROT>(P, s);                             \
   }
 
 // Storage combinations: the caller's FP32 or FP16 image in, FP32
 // intermediates between layers (sv_filter), FP32 / FP16 RGBA intermediates
 // (image adjoint's recomputation, no-allocation filter), the caller's
 // image out.
-#define DISK_SV_INSTANTIATE(DIMS, TAPS, ROT)                                                \
+#define DISK_SV_INSTANTIATE(DIMS, ROT)                                                      \
   template <>                                                                               \
-  int launch_sv_layer<DIMS, TAPS, ROT>(int src, int dst, int C, const SvLayerParams &P,       \
-                                       cudaStream_t s, int pix) {                           \
+  int launch_sv_layer<DIMS, ROT>(int src, int dst, int C, const SvLayerParams &P,           \
+                                 cudaStream_t s, int pix) {                                 \
     const bool c4 = C == 4;                                                                 \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F32, PIX_RGBA32)                                        \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA32, PIX_RGBA32)                                     \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA32, PIX_F32)                                        \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F32, PIX_F32)                                           \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_RGBA16)                                        \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA16, PIX_RGBA16)                                     \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_RGBA16, PIX_F16)                                        \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_F16)                                           \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F16, PIX_F32)                                           \
-    DISK_SV_CASE(DIMS, TAPS, ROT, PIX_F32, PIX_F16)                                           \
+    DISK_SV_CASE(DIMS, ROT, PIX_F32, PIX_RGBA32)                                            \
+    DISK_SV_CASE(DIMS, ROT, PIX_RGBA32, PIX_RGBA32)                                         \
+    DISK_SV_CASE(DIMS, ROT, PIX_RGBA32, PIX_F32)                                            \
+    DISK_SV_CASE(DIMS, ROT, PIX_F32, PIX_F32)                                               \
+    DISK_SV_CASE(DIMS, ROT, PIX_F16, PIX_RGBA16)                                            \
+    DISK_SV_CASE(DIMS, ROT, PIX_RGBA16, PIX_RGBA16)                                         \
+    DISK_SV_CASE(DIMS, ROT, PIX_RGBA16, PIX_F16)                                            \
+    DISK_SV_CASE(DIMS, ROT, PIX_F16, PIX_F16)                                               \
+    DISK_SV_CASE(DIMS, ROT, PIX_F16, PIX_F32)                                               \
+    DISK_SV_CASE(DIMS, ROT, PIX_F32, PIX_F16)                                               \
     return fail(DISK_ERR_INVALID_ARG, "unsupported layer storage combination");            \
   }
 

@@ -2,5 +2,5 @@
 #include "sv_layer.cuh"
 
 namespace disk {
-DISK_SV_INSTANTIATE(1, kSvTapsShared, true)
+DISK_SV_INSTANTIATE(1, true)
 }  // namespace disk

@@ -2,5 +2,5 @@
 #include "sv_layer.cuh"
 
 namespace disk {
-DISK_SV_INSTANTIATE(2, kSvTapsShared, true)
+DISK_SV_INSTANTIATE(2, true)
 }  // namespace disk
