@@ -250,14 +250,15 @@ struct FitShared {
 
 namespace cg = cooperative_groups;
 
-// Barrier over the CTAs that share a target (release / acquire at cluster
-// scope, global writes fenced first); a plain block barrier when CL == 1.
+// Barrier over the CTAs that share a target; a plain block barrier when
+// CL == 1.  The cluster barrier's arrive has release and its wait acquire
+// semantics at cluster scope, which orders the CTAs' global canvas writes
+// before the other CTAs' reads with no separate fence.
 template <int CL>
 __device__ __forceinline__ void target_sync() {
   if (CL == 1) {
     __syncthreads();
   } else {
-    __threadfence();
     cg::this_cluster().sync();
   }
 }
