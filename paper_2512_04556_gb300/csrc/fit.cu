@@ -243,9 +243,12 @@ struct FitShared {
   PreparedTaps pt;  // the layer being swept
   float red[kFitMaxWarps];
   float closs;  // this CTA's share of the loss
-  // per-(chunk, tap) partial tap gradients of the warps of this CTA
-  float part[3 * (kFitMaxWarps * kFitMaxCluster > DISK_MAX_TAPS ? kFitMaxWarps * kFitMaxCluster
-                                                                   : DISK_MAX_TAPS)];
+  // per-(chunk, tap) partial tap gradients of the warps of this CTA, two
+  // buffers used by alternate layers
+  static constexpr int kPart = 3 * (kFitMaxWarps * kFitMaxCluster > DISK_MAX_TAPS
+                                        ? kFitMaxWarps * kFitMaxCluster
+                                        : DISK_MAX_TAPS);
+  float part[2 * kPart];
 };
 
 namespace cg = cooperative_groups;
@@ -362,6 +365,9 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
   for (int l = L - 1; l >= 0; --l) {
     const int S = sh.ext[l].S, halo = sh.ext[l].H;
     const float *prev = act[l];
+    // this layer's partial-sum buffer: the other one may still be read by
+    // the cluster's CTAs summing the previous layer
+    float *part = sh.part + (l & 1) * FitShared::kPart;
     // dL/dw, dL/do of every tap of layer l: `chunks` warps of the cluster
     // per tap (every warp works when T is below the warp count), each over
     // every chunks-th row of the support box, lanes over its pixels.  Unit
@@ -390,29 +396,31 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
       }
       gw = warp_sum(gw); gdx = warp_sum(gdx); gdy = warp_sum(gdy);
       if (lane == 0) {
-        float *pp = sh.part + (size_t)wi * 3;
+        float *pp = part + (size_t)wi * 3;
         pp[0] = gdx * t.z; pp[1] = gdy * t.z; pp[2] = gw;
       }
     }
+    if (l > 0) {
+      // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
+      // (reads G like the tap gradients above, writes the other plane)
+      prepare_taps(sh.pt, sh.taps + l * T, T, halo, -1.f, R);
+      __syncthreads();
+      canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.pt, T, tid, nthr);
+    }
+    // the partial sums and the adjoint plane are complete everywhere
     target_sync<CL>();
     for (int j = threadIdx.x; j < T * 3; j += blockDim.x) {
       const int i = j / 3, k = j % 3;
       float acc = 0.f;
       for (int c = 0; c < chunks; ++c) {
         const int wi = c * T + i;
-        acc += rank_ptr<CL>(sh.part, (unsigned)((wi % nwt) / nw))[(size_t)wi * 3 + k];
+        acc += rank_ptr<CL>(part, (unsigned)((wi % nwt) / nw))[(size_t)wi * 3 + k];
       }
       sh.g[(size_t)l * T * 3 + j] = acc;
     }
-    if (l > 0) {
-      // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
-      prepare_taps(sh.pt, sh.taps + l * T, T, halo, -1.f, R);
-      __syncthreads();
-      canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.pt, T, tid, nthr);
-    }
-    target_sync<CL>();  // the adjoint plane is whole; every CTA has read the partial sums
     float *t = G; G = Gn; Gn = t;
   }
+  __syncthreads();  // sh.g complete for the update
 }
 
 template <int NT, int CL>
