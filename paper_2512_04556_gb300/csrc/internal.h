@@ -25,8 +25,8 @@ struct disk_basis {
   float4 *d_taps = nullptr;      // [L][B][T] = (dx, dy, w, w)
   // the same taps in the pair layout of the 3-channel filter (same shape;
   // for each node, slot 2j = (dx_2j, dx_2j+1, dy_2j, dy_2j+1) and slot
-  // 2j + 1 = (w_2j, w_2j+1, w_2j, w_2j+1); an odd T's last slot as above);
-  // it shares d_taps' allocation
+  // 2j + 1 = (w_2j, w_2j+1) of the node, then of its successor on axis 0;
+  // an odd T's last slot as above); it shares d_taps' allocation
   float4 *d_taps_pair = nullptr;
   // filter tile configuration (pixels per thread) of every layer, chosen by
   // disk_sv_filter_autotune per (H, W, C, dtype | rotated << 8); read by
