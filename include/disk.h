@@ -179,10 +179,12 @@ int disk_sv_filter_backward(const disk_basis *basis, const void *d_in, size_t in
  * application that owns the whole device-memory budget, a real-time loop that
  * forbids allocation after start-up so that its latency stays bounded, or
  * code that runs where the allocator may not be re-entered.  This entry point
- * computes exactly what disk_sv_filter computes, with the same arguments,
- * layouts and status codes, but calls no cudaMalloc, cudaFree or other
- * allocating routine: the intermediate layers live in one fixed array built
- * into the library (two FP32 RGBA planes, 32 MiB), which every device that
+ * runs disk_sv_filter's own code path (argument checks, the per-layer tile
+ * record of disk_sv_filter_autotune, tensor-memory-accelerator copies, FP32
+ * intermediates) and so returns disk_sv_filter's results bit for bit, with
+ * the same arguments, layouts and status codes, but calls no cudaMalloc,
+ * cudaFree or other allocating routine: the two intermediate planes live in
+ * one fixed 32 MiB array built into the library, which every device that
  * loads the library holds until the process exits.
  * Limit: H * W <= 1048576 pixels; larger images return DISK_ERR_UNSUPPORTED
  *   before any work is queued.

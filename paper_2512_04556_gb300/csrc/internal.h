@@ -90,6 +90,14 @@ int validate_image_args(const void *d_in, size_t in_pitch, const void *d_out,
                         const float *d_maps);
 int validate_nodes(int dims, const int *n_nodes, const float *node_vals);
 
+// disk_sv_filter with the two intermediate planes given by the caller
+// (H * f32_mid_pitch(W, C) bytes each, 16-byte aligned; plane1 unused for
+// L <= 2, both unused for L = 1): the same argument checks, tile choice,
+// tensor copies and kernels, and no allocation.  Returns a DISK_* status.
+int sv_filter_given_planes(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
+                           size_t out_pitch, int H, int W, int C, int dtype,
+                           const float *d_maps, void *plane0, void *plane1, cudaStream_t s);
+
 }  // namespace disk
 
 #define DISK_TRY_CUDA(expr, what)                   \

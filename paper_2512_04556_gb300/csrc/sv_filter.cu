@@ -128,7 +128,10 @@ bool encode_rows(EncodeTiled fn, CUtensorMap *m, const void *base, long long wid
 
 int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
                size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
-               const float *d_angle, cudaStream_t s, const int *pix, cudaEvent_t *ev) {
+               const float *d_angle, cudaStream_t s, const int *pix, cudaEvent_t *ev,
+               void *const *given = nullptr) {
+  // given (optional): two caller-owned intermediate planes of
+  // H * f32_mid_pitch(W, C) bytes each, used instead of pool scratch.
   // The parameter block is large; keep it off the host stack.
   static thread_local SvLayerParams P;
   P.maps = d_maps;
@@ -145,7 +148,8 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
   const EncodeTiled encode = encode_tiled();
   void *bufs[2] = {nullptr, nullptr};
   const size_t plane = (size_t)H * mid_pitch;
-  const int nbuf = L >= 3 ? 2 : (L == 2 ? 1 : 0);
+  const int nbuf = given ? 0 : (L >= 3 ? 2 : (L == 2 ? 1 : 0));
+  if (given) { bufs[0] = given[0]; bufs[1] = given[1]; }
   for (int i = 0; i < nbuf; ++i) {
     cudaError_t e = scratch_alloc(&bufs[i], plane, s);
     if (e != cudaSuccess) {
@@ -299,6 +303,18 @@ int autotune(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out
 }
 
 }  // namespace
+
+int sv_filter_given_planes(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
+                           size_t out_pitch, int H, int W, int C, int dtype,
+                           const float *d_maps, void *plane0, void *plane1, cudaStream_t s) {
+  int rc = check_filter_args(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps);
+  if (rc) return rc;
+  const std::vector<int> pix = layer_pix(b, H, W, C, dtype, false);
+  void *const planes[2] = {plane0, plane1};
+  return run_filter(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, nullptr, s,
+                    pix.data(), nullptr, planes);
+}
+
 }  // namespace disk
 
 using namespace disk;

@@ -1,7 +1,9 @@
 // disk_sv_filter_noalloc: the spatially varying filter for callers that may
-// not allocate device memory.  Same kernels and results as disk_sv_filter;
-// the intermediate layers live in a fixed array compiled into the library
-// instead of memory taken from the stream's pool.
+// not allocate device memory.  It runs disk_sv_filter's own code path (the
+// same checks, per-layer tile choice, tensor copies, kernels and FP32
+// intermediate layout) with the two intermediate planes placed in a fixed
+// array compiled into the library instead of memory taken from the pool, so
+// its results equal disk_sv_filter's bit for bit.
 #include <mutex>
 
 #include "sv_layer.cuh"
@@ -11,10 +13,13 @@ namespace {
 
 constexpr long long kNoAllocMaxPixels = 1ll << 20;  // H * W limit: 1,048,576 pixels
 
-// Room for two FP32 RGBA intermediate planes of up to kNoAllocMaxPixels
-// pixels each (FP16 images use FP16 planes and half of it): 32 MiB that every
-// device which loads the library holds until the process exits.  Every layer overwrites each pixel of its plane before the next
-// layer reads it, so nothing needs clearing between calls.
+// Two FP32 intermediate planes of up to kNoAllocMaxPixels pixels: a plane
+// has rows of f32_mid_pitch(W, C) bytes, at most 16 W for C <= 4 (16 W is a
+// multiple of 16 and at least 4 C W), so a plane needs at most 16 MiB and
+// plane 1 starts at the array's half.  32 MiB that every device which loads
+// the library holds until the process exits.  Every layer overwrites each
+// pixel of its plane before the next layer reads it, so nothing needs
+// clearing between calls.
 static __device__ __align__(256) float4 g_noalloc_planes[2 * kNoAllocMaxPixels];
 
 constexpr int kMaxDevices = 64;
@@ -37,43 +42,6 @@ int planes_address(int dev, float4 **out) {
   return DISK_OK;
 }
 
-int run_noalloc(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
-                size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
-                float4 *planes, cudaStream_t s) {
-  static thread_local SvLayerParams P;
-  P.maps = d_maps;
-  P.rot = nullptr;
-  P.use_tma = 0;
-  P.err = device_error_word();
-  P.H = H; P.W = W; P.C = C; P.T = b->T;
-  make_axes(b->dims, b->n_nodes, b->node_vals.data(), P.ax);
-  const int user = dtype == DISK_F32 ? PIX_F32 : PIX_F16;
-  const int mid = intermediate_kind(dtype);
-  const size_t mid_bytes = kind_bytes(mid);
-  const int L = b->L;
-  // plane 0 at the start of the array, plane 1 after H * W pixels of the
-  // intermediate kind (both fit: the array holds two FP32 RGBA planes)
-  char *bufs[2] = {reinterpret_cast<char *>(planes),
-                   reinterpret_cast<char *>(planes) + (size_t)H * W * mid_bytes};
-  int rc = DISK_OK;
-  for (int l = 0; l < L && rc == DISK_OK; ++l) {
-    P.halo = P.halo_x = halo_of(b->reach[l]);
-    P.region_w = kSvTileW + 2 * P.halo;
-    const int src = l == 0 ? user : mid;
-    const int dst = l == L - 1 ? user : mid;
-    P.src = l == 0 ? d_in : bufs[(l - 1) & 1];
-    P.src_pitch = l == 0 ? (long long)in_pitch : (long long)(W * mid_bytes);
-    P.dst = l == L - 1 ? d_out : bufs[l & 1];
-    P.dst_pitch = l == L - 1 ? (long long)out_pitch : (long long)(W * mid_bytes);
-    P.gtaps = layer_taps(b, l, C);
-    P.bt = b->B * b->T;
-    const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(kSvDefaultPix) + 2 * P.halo), C);
-    P.tap_cap = sv_tap_cap(b->dims, b->n_nodes[1], b->B, b->T, region);
-    rc = launch_layer(b->dims, false, src, dst, C, P, s, kSvDefaultPix);
-  }
-  return rc;
-}
-
 }  // namespace
 }  // namespace disk
 
@@ -90,14 +58,13 @@ extern "C" int disk_sv_filter_noalloc(const disk_basis *b, const void *d_in, siz
   int dev = 0;
   DISK_TRY_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   if (dev != b->device) return fail(DISK_ERR_INVALID_ARG, "basis lives on another device");
-  for (int l = 0; l < b->L; ++l) {
-    const int h = halo_of(b->reach[l]);
-    const size_t smem = sv_smem_bytes((size_t)(kSvTileW + 2 * h) * (sv_tile_h(kSvDefaultPix) + 2 * h), C);
-    if (smem > (size_t)kSvMaxSmem) return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory");
-  }
   float4 *planes = nullptr;
   rc = planes_address(dev, &planes);
   if (rc) return rc;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return run_noalloc(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, planes, s);
+  // The device status word that the layer kernels report bounded-wait
+  // timeouts in was allocated when the basis was created on this device, so
+  // the call below allocates nothing.
+  return sv_filter_given_planes(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps,
+                                planes, planes + kNoAllocMaxPixels,
+                                static_cast<cudaStream_t>(stream));
 }
