@@ -37,11 +37,31 @@ NOMINAL_HBM_GBS = 8000.0
 # (12), the integer/fraction split of the offset (4), the four bilinear
 # corner weights times w (8) and the 4 corners x 3 channels of Eq. 2 (12).
 OPS_PER_PX_TAP = 36
-# FP32 lanes: 152 SMs x 128 lanes, one operation per lane per clock.
-SMS, FP32_LANES_PER_SM = 152, 128
-# DRAM bytes (read + write) of one pass (the L = 4 sv_layer launches) of the
-# current kernel, from an ncu capture of it; None whenever the kernel changes.
-TRAFFIC_PER_PASS = 845.5e6
+# FP32 lanes per SM (one operation per lane per clock); the SM count comes
+# from the device.
+FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) of one pass (the L sv_layer launches) from an
+# ncu capture, tagged with the hash of the filter kernel's sources at the
+# capture; reported as null once the sources differ.
+TRAFFIC_PER_PASS = {"bytes": None, "sources_sha16": None, "capture": None}
+KERNEL_SOURCES = ("sv_layer.cuh", "sv_common.cuh", "sv_layer_2d.cu", "sv_filter.cu")
+
+
+def kernel_sources_sha16() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2512_04556_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """The captured DRAM bytes per pass if they belong to these sources."""
+    t = TRAFFIC_PER_PASS
+    if t["bytes"] is None or t["sources_sha16"] != kernel_sources_sha16():
+        return None
+    return t["bytes"]
 
 
 def parse():
@@ -199,33 +219,46 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
         peaks = json.load(open(pk))
     hbm = peaks.get("hbm_gbs")
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     out = {}
     # The gather is bound by FP32 arithmetic and instruction issue, not by
     # HBM: the roofline is the FP32 lane throughput at the maximum SM clock.
+    # Its arithmetic floor: taps x OPS_PER_PX_TAP operations per pixel at the
+    # full lane rate bound the pixel rate, and so the HBM rate of the fused
+    # pass's algorithmic bytes, far below the HBM peak.
     taps = basis.L * basis.T
-    peak_tops = SMS * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    peak_tops = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     achieved_tops = px * taps * OPS_PER_PX_TAP / (ms * 1e-3) / 1e12
     achieved_gbs = BYTES_PER_PX * px / (ms * 1e-3) / 1e9
+    hbm_peak = hbm or 6800.0
+    ceiling_gbs = peak_tops * 1e12 / (taps * OPS_PER_PX_TAP) * BYTES_PER_PX / 1e9
     out["roofline"] = {
         "bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Top/s",
         "frac": achieved_tops / peak_tops,
-        "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz",
-        "ops_per_px_tap": OPS_PER_PX_TAP, "taps_per_px": taps, "traffic": TRAFFIC_PER_PASS,
+        "peak_source": f"derived: {sms} SMs (device) x {FP32_LANES_PER_SM} FP32 lanes x "
+                       f"{sm_mhz:.0f} MHz (max SM clock, MEASURED_PEAKS.json)",
+        "ops_per_px_tap": OPS_PER_PX_TAP, "taps_per_px": taps,
+        "traffic": recorded_traffic(), "traffic_unit": "bytes per pass (ncu)",
+        "kernel_sources_sha16": kernel_sources_sha16(),
         "kernel": "sv_layer_kernel (all L launches of one pass)",
-        "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm or 6800.0,
-                "frac": achieved_gbs / (hbm or 6800.0),
+        "hbm_frac": achieved_gbs / hbm_peak,
+        "hbm_frac_nominal_8tbs": achieved_gbs / NOMINAL_HBM_GBS,
+        "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": hbm_peak,
+                "frac": achieved_gbs / hbm_peak,
                 "peak_source": "measured" if hbm else "fallback",
-                "bytes_per_px": BYTES_PER_PX}}
+                "bytes_per_px": BYTES_PER_PX,
+                "arithmetic_ceiling_gbs": ceiling_gbs,
+                "arithmetic_ceiling_frac": ceiling_gbs / hbm_peak}}
     # shared-memory model: every tap reads four corners of 3 FP32 channels
     # from the staged region (the kernel reuses a pixel's bottom corners as
     # the next pixel's top corners when they coincide, so it reads fewer);
     # peak: 128 bytes per clock per SM
     smem_bytes = px * taps * 4 * 12
     smem_gbs = smem_bytes / (ms * 1e-3) / 1e9
-    smem_peak = SMS * 128 * sm_mhz * 1e6 / 1e9
+    smem_peak = sms * 128 * sm_mhz * 1e6 / 1e9
     out["smem_model"] = {"bytes_per_pass": smem_bytes, "achieved_gbs": smem_gbs,
                          "peak_gbs": smem_peak, "frac": smem_gbs / smem_peak,
-                         "peak_source": f"derived: {SMS} SMs x 128 B x {sm_mhz:.0f} MHz"}
+                         "peak_source": f"derived: {sms} SMs x 128 B x {sm_mhz:.0f} MHz"}
 
     # end to end through the public API with host buffers: the frame pipeline
     # copies every frame's image and maps in and its result out, the copies of
@@ -319,6 +352,7 @@ def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
     dd = d_dense.float()
     mse = float(((o - dd) ** 2).mean().item())
     out["fit"] = fit_leg(stream)
+    out["learned_init"] = learned_init_leg()
     out["gaussian_tilt_shift"] = gaussian_leg(d_img, flush, stream)
     out["bokeh_1080p_fp32"] = bokeh1080_leg(flush, stream)
     out["small_256_fp32"] = small256_leg(stream)
@@ -555,6 +589,28 @@ def fit_leg(stream, steps=500, batch=256, reps=3):
             "targets": "seeded polygons, rings, 5-8 point stars, annuli; odd sizes 33..129"}
 
 
+def learned_init_leg():
+    """The learned initializer at its full size: 50k training pairs from the
+    batched fitter (Eq. 6 start, 500 steps, seeded non-convex targets of odd
+    sizes 33..129), the 4096-512-512-512-192 network trained 30 epochs on the
+    GPU by the library's kernels, then 2k held-out targets (a disjoint index
+    range): median Adam steps of the learned start plus refinement to reach
+    each target's plain 500-step loss."""
+    import torch
+
+    from paper_2512_04556_gb300 import learned_init as li
+    c = wl.C5
+    t0 = time.perf_counter()
+    res = li.run(n_train=c["train"], n_heldout=c["heldout"], epochs=30, steps=500,
+                 hidden=c["hidden"], depth=c["depth"])
+    torch.cuda.synchronize()
+    res["total_s"] = time.perf_counter() - t0
+    res["target_speedup"] = 5.0
+    res["config"] = (f"{c['train']} pairs, {c['heldout']} held-out, L={c['L']} T={c['T']}, "
+                     f"input {c['side']}x{c['side']}")
+    return res
+
+
 def fit_cpu_baseline(budget_s=10.0):
     """The oracle's fitter (FP64, one target at a time) on the first targets
     of the same batch, 500 steps each."""
@@ -648,6 +704,7 @@ def main():
         line = dict(base, value=res["value"], ms_per_step=res["ms_per_step"],
                     clocks=res["clocks"], gpu_launches=res["gpu_launches"])
         for k in ("roofline", "e2e", "dense_sv", "backward_image", "backward_full", "fit",
+                  "learned_init",
                   "gaussian_tilt_shift",
                   "bokeh_1080p_fp32", "small_256_fp32",
                   "radial_motion", "rotational_bokeh", "smem_model"):

@@ -428,6 +428,31 @@ int disk_mlp_adam(float *d_params, float *d_m, float *d_v, const float *d_grad, 
 int disk_downsample_targets(const float *d_targets, const int *sizes, int batch,
                             int side, float *d_out, void *stream);
 
+/* The learned start of the fit, every step on the device.  The paper starts
+ * the Eq. 4 fit from Eq. 6 rings or Eq. 7 sparse samples (Sec. 4.1-4.2);
+ * this project adds the network above and uses the fitted loss to judge it:
+ *   1. each target is area-resampled to side x side (disk_downsample_targets);
+ *   2. the network (d_params, n_in = side * side, `hidden`, `depth`,
+ *      n_out = L * T * 3) maps it to network units;
+ *   3. network units -> pixels: offsets clamped to [-1, 1] and multiplied by
+ *      the half-width s_b = max(1, (K_b - 1) / 2), weights divided by T;
+ *   4. the Eq. 6 start is built as disk_fit does for DISK_INIT_IR;
+ *   5. the loss (`loss`, `eps` as in disk_fit) of both starts is evaluated,
+ *      and per target the network start is kept if its loss is <= the Eq. 6
+ *      start's (a NaN loss keeps the Eq. 6 start).
+ * d_targets, sizes, batch, L, T: as disk_fit (sizes odd, <= 257).
+ * d_theta_out: float [batch][L][T][3] (pixels, device, caller-owned): the
+ *   chosen start, ready for disk_fit with DISK_INIT_GIVEN.
+ * d_used_network: int [batch] (device, may be NULL): 1 where the network
+ *   start was kept, else 0.
+ * Scratch: batch * (side^2 + 4 L T 3 + 3) floats from the library's memory
+ * pool.  Copies a small per-target table from pageable host memory (not
+ * capturable in a graph).  Errors: DISK_ERR_INVALID_ARG for null pointers,
+ * bad shapes or even sizes; otherwise those of the steps it runs. */
+int disk_learned_init(const float *d_targets, const int *sizes, int batch, int L, int T,
+                      const float *d_params, int side, int hidden, int depth, int loss,
+                      float eps, float *d_theta_out, int *d_used_network, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,8 +21,13 @@ class SVFilterFunction(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_out):
+        # The library takes the incoming gradient in its own precision (FP32
+        # or FP16) and returns the image gradient in FP32; autograd then
+        # stores it in the image's dtype (one rounding for an FP16 image, as
+        # for any FP16 leaf).  disk.sv_filter_backward_image gives the FP32
+        # gradient directly.
         (maps,) = ctx.saved_tensors
-        g = disk.sv_filter_backward_image(ctx.basis, grad_out.contiguous().to(ctx.img_dtype), maps)
+        g = disk.sv_filter_backward_image(ctx.basis, grad_out.contiguous(), maps)
         return g.to(ctx.img_dtype), None, None
 
 

@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
             "disk_mlp_adam": (_i, [_vp, _vp, _vp, _vp, _i, ctypes.c_float, _i, _i, _i, _i, _vp]),
             "disk_fit_loss_grad": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _vp, _vp, _vp,
                                         _vp]),
+            "disk_learned_init": (_i, [_vp, _ip, _i, _i, _i, _vp, _i, _i, _i, _i,
+                                       ctypes.c_float, _vp, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(l, name)
@@ -533,3 +535,21 @@ def downsample_targets(packed, sizes, side: int = 64, stream=None):
         _vp(packed.data_ptr()), _int_arr(sizes), len(sizes), side, _vp(out.data_ptr()),
         _stream(stream)))
     return out
+
+
+def learned_init(net: "MLP", packed, sizes, L: int, T: int, side: int = 64,
+                 loss: int = LOSS_MSE, eps: float = 0.0, stream=None):
+    """disk_learned_init: the network's start for each target (pixels), or the
+    Eq. 6 start where that has the lower fitted loss.  Returns
+    (theta [batch, L, T, 3], used_network [batch] bool), both on the device."""
+    import torch
+    n_in, hidden, depth, n_out = net.shape
+    if n_in != side * side or n_out != L * T * 3:
+        raise ValueError(f"network shape {net.shape} does not fit side={side}, L={L}, T={T}")
+    theta = torch.empty((len(sizes), L, T, 3), device=packed.device, dtype=torch.float32)
+    used = torch.empty(len(sizes), device=packed.device, dtype=torch.int32)
+    _check("disk_learned_init", lib().disk_learned_init(
+        _vp(packed.data_ptr()), _int_arr(sizes), len(sizes), L, T, _vp(net.params.data_ptr()),
+        side, hidden, depth, loss, eps, _vp(theta.data_ptr()), _vp(used.data_ptr()),
+        _stream(stream)))
+    return theta, used.bool()

@@ -68,17 +68,6 @@ def to_labels(theta, sizes, T):
     return y.reshape(theta.shape[0], -1)
 
 
-def from_labels(y, sizes, L, T):
-    """Network units -> pixels, offsets clamped to the fit's box |o| <= s."""
-    import torch
-    s = torch.from_numpy(_scales(sizes)).to(y.device)[:, None, None]
-    th = y.reshape(-1, L, T, 3).clone()
-    th[..., 0] = th[..., 0].clamp(-1, 1) * s
-    th[..., 1] = th[..., 1].clamp(-1, 1) * s
-    th[..., 2] /= T
-    return th.contiguous()
-
-
 def train(net, X, Y, epochs=30, batch=256, lr0=1e-3, lr1=1e-5, seed=0, log=None):
     """Adam on shuffled mini-batches, lr decayed geometrically lr0 -> lr1."""
     import torch
@@ -100,16 +89,10 @@ def train(net, X, Y, epochs=30, batch=256, lr0=1e-3, lr1=1e-5, seed=0, log=None)
 
 def network_start(net, targets, L, T, loss=disk.LOSS_MSE):
     """The network's complexes [n, L, T, 3] (pixels), each replaced by the
-    Eq. 6 radial start where that has the lower fitted loss."""
-    import torch
+    Eq. 6 radial start where that has the lower fitted loss
+    (disk_learned_init, every step on the device)."""
     packed, sizes = disk.pack_targets(targets)
-    X = disk.downsample_targets(packed, sizes, SIDE).reshape(len(sizes), -1)
-    th_net = from_labels(net.forward(X), sizes, L, T)
-    th_ir, _, _ = disk.fit(packed, sizes, L, T, 0, init=disk.INIT_IR)
-    l_net, _ = disk.fit_loss_grad(packed, sizes, th_net, loss=loss)
-    l_ir, _ = disk.fit_loss_grad(packed, sizes, th_ir, loss=loss)
-    use_net = (l_net <= l_ir)[:, None, None, None]
-    return torch.where(use_net, th_net, th_ir).contiguous(), use_net.reshape(-1)
+    return disk.learned_init(net, packed, sizes, L, T, SIDE, loss=loss)
 
 
 def iterations_to_reach(hist, ref):

@@ -56,7 +56,7 @@ def test_area_resampling_matches_oracle(torch_cuda):
         assert np.abs(out[b] - want).max() <= 1e-5, b
 
 
-def test_learned_initializer_gains_over_the_radial_start(torch_cuda):
+def test_learned_initializer_gains_over_the_radial_start(torch_cuda, capsys):
     """A small learned initializer (training pairs from the project's own
     fitter) reaches the plain fitter's final loss in fewer Adam steps on
     held-out targets than the paper's radial start needs (its full run)."""
@@ -71,7 +71,11 @@ def test_learned_initializer_gains_over_the_radial_start(torch_cuda):
     net = disk.MLP(li.SIDE * li.SIDE, 256, 2, L * T * 3, seed=1)
     li.train(net, X, Y, epochs=20, batch=128)
     res = li.evaluate(net, held_t, L, T, steps)
-    assert res["median_iterations"] < steps, res
+    with capsys.disabled():
+        print("\nlearned-init gain (toy config):", res)
+    # this toy configuration (3,000 pairs, L = 3, T = 8, 200 steps) gains
+    # about 1.45x; the floor is 1.25x fewer steps
+    assert res["speedup"] >= 1.25, res
     assert res["median_start_loss_ratio"] < 1.0, res
 
 
@@ -99,3 +103,48 @@ def test_grad_matches_oracle_and_halves_average_to_full_batch(torch_cuda):
     a.apply(avg, 1e-3)
     b.train_step(xd, td, 1e-3)
     assert (a.params - b.params).abs().max().item() <= 1e-6
+
+
+def _composed_learned_start(torch, net, packed, sizes, L, T):
+    """The learned start assembled from the other entry points and torch
+    arithmetic: resample, forward, network units -> pixels, Eq. 6 start, the
+    fitted loss of both, the lower one kept (network on a tie)."""
+    from paper_2512_04556_gb300 import disk
+    X = disk.downsample_targets(packed, sizes, 64).reshape(len(sizes), -1)
+    y = net.forward(X).reshape(-1, L, T, 3)
+    s = torch.tensor([max(1.0, (k - 1) / 2) for k in sizes], dtype=torch.float32,
+                     device=y.device)[:, None, None]
+    th_net = torch.stack([y[..., 0].clamp(-1, 1) * s, y[..., 1].clamp(-1, 1) * s, y[..., 2] / T],
+                         dim=-1).contiguous()
+    th_ir = disk.fit(packed, sizes, L, T, 0, init=disk.INIT_IR)[0]
+    l_net, _ = disk.fit_loss_grad(packed, sizes, th_net)
+    l_ir, _ = disk.fit_loss_grad(packed, sizes, th_ir)
+    keep = l_net <= l_ir
+    return torch.where(keep[:, None, None, None], th_net, th_ir), keep
+
+
+def test_learned_init_entry_point_equals_its_steps(torch_cuda):
+    """disk_learned_init (all steps on the device behind the C ABI) gives the
+    composed pipeline's starts bit for bit, for a random network and for one
+    whose output is the single-point complex (all taps at 0, weights 1/T):
+    that start is exact on a one-pixel target and worse than the Eq. 6 ring
+    on broad ones, so both branches of the choice are taken."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    L, T = 2, 4
+    point = np.zeros((17, 17), np.float32)
+    point[8, 8] = 1.0
+    tg = wl.shape_batch(30, kmin=17, kmax=45, first=900) + [point, wl.disk(9.0)]
+    packed, sizes = disk.pack_targets(tg)
+    rand_net = disk.MLP(64 * 64, 64, 2, L * T * 3, seed=3)
+    point_net = disk.MLP(64 * 64, 64, 2, L * T * 3, seed=3)
+    point_net.params.zero_()
+    bias = torch.zeros((L, T, 3), device="cuda")
+    bias[..., 2] = 1.0                       # weight label w * T = 1
+    point_net.params[-L * T * 3:] = bias.reshape(-1)
+    for net in (rand_net, point_net):
+        got, used = disk.learned_init(net, packed, sizes, L, T)
+        want, keep = _composed_learned_start(torch, net, packed, sizes, L, T)
+        assert torch.equal(used, keep)
+        assert torch.equal(got, want)
+    assert bool(used[-2]) and not bool(used[-1])

@@ -87,6 +87,29 @@ def test_autograd_function_image_gradient(torch_cuda):
     assert err <= TOL
 
 
+def test_autograd_function_image_gradient_fp16_storage(torch_cuda):
+    """FP16 image: the incoming FP16 gradient reaches the library unchanged,
+    the library's FP32 image gradient matches the FP64 transpose at the FP32
+    gate, and autograd rounds it to FP16 once (within one FP16 unit of the
+    rounded oracle)."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import autograd, disk
+    H, W = 37, 52
+    axes, th, maps = _case(H, W, 2, 19)
+    b = disk.Basis.from_arrays(axes, th)
+    img = torch.rand((H, W, 3), device="cuda").half().requires_grad_()
+    dm = torch.from_numpy(maps).cuda()
+    w = torch.rand((H, W, 3), device="cuda").half()
+    (autograd.sv_filter(img, dm, b) * w).sum().backward()
+    want = _oracle_adjoint(w.float().cpu().numpy(), maps, axes, th)
+    g32 = disk.sv_filter_backward_image(b, w, dm).cpu().numpy()
+    assert np.abs(g32 - want).max() / np.abs(want).max() <= TOL
+    assert img.grad.dtype == torch.float16
+    want16 = want.astype(np.float16).astype(np.float64)
+    err = np.abs(img.grad.cpu().numpy().astype(np.float64) - want16).max() / np.abs(want).max()
+    assert err <= 2.0 ** -10
+
+
 @pytest.mark.parametrize("dims,H,W,C", [(1, 29, 41, 3), (2, 35, 30, 3), (1, 20, 64, 4)])
 def test_theta_gradient_matches_oracle(torch_cuda, dims, H, W, C):
     torch = torch_cuda
