@@ -204,11 +204,20 @@ int disk_sv_filter_noalloc(const disk_basis *basis, const void *d_in,
 /* Tile autotuner of disk_sv_filter: runs the filter on these buffers with
  * each built tile configuration (2 or 4 pixels per thread: 32 x 16 or
  * 32 x 32 output tiles), times every layer of each (the best tile depends
- * on the layer's halo), and records the fastest per layer in the basis
- * handle for this (H, W, C, dtype); later disk_sv_filter calls with that
- * shape use it (without a record: 32 x 16 everywhere).  Writes d_out.
+ * on the layer's halo), then times every adjacent pair of layers fused into
+ * one launch -- the layer-fused form of the cascade (Sec. 3.2 Eq. 3): a
+ * 32 x 16 tile stages the first layer's source on the tile grown by both
+ * layers' halos, computes the first layer on the tile grown by the second
+ * layer's halo into shared memory and the second layer from there, so the
+ * intermediate between them never leaves the chip, at the price of
+ * recomputing the first layer on the grown region -- and records, in the
+ * basis handle for this (H, W, C, dtype), the fastest cover of the layers by
+ * single layers and fused pairs; later disk_sv_filter calls with that shape
+ * use it (without a record: 32 x 16 single layers).  Writes d_out.
  * Synchronises the stream (do not call while capturing a graph).  chosen
- * (may be NULL; int[L]) receives the pixels per thread of every layer. */
+ * (may be NULL; int[L]) receives every layer's code: 2 or 4 (pixels per
+ * thread of a single-layer launch), 8 (first layer of a fused pair, 32 x 16
+ * tiles) followed by 0 (second layer of that pair). */
 int disk_sv_filter_autotune(const disk_basis *basis, const void *d_in, size_t in_pitch,
                             void *d_out, size_t out_pitch, int H, int W, int C,
                             int dtype, const float *d_maps, int *chosen, void *stream);
@@ -272,6 +281,14 @@ int disk_device_status(void *stream);
  * Asynchronous on `stream`. */
 int disk_selftest_bounded_wait(long long iterations, void *stream);
 
+/* Records every layer's launch choice for disk_sv_filter at this (H, W, C,
+ * dtype) in the basis handle: choice int[L] with the codes that
+ * disk_sv_filter_autotune reports (2 or 4; 8 followed by 0 for a fused
+ * pair).  DISK_ERR_INVALID_ARG for other codes or an 8 not followed by 0;
+ * DISK_ERR_UNSUPPORTED where a tile or pair does not fit shared memory. */
+int disk_sv_filter_set_layers(const disk_basis *basis, int H, int W, int C, int dtype,
+                              const int *choice);
+
 /* Records one tile configuration (pixels per thread: 2 or 4) for every
  * layer, for this (H, W, C, dtype), in the basis handle. */
 int disk_sv_filter_set_tile(const disk_basis *basis, int H, int W, int C, int dtype,
@@ -329,9 +346,11 @@ int disk_synth_kernel(const float *d_theta, int batch, int L, int T, int K,
  * d_final_loss: float [batch], loss at the result (may be NULL).
  * d_loss_hist: float [batch][steps+1], loss before every step and after the
  *   last (may be NULL).
- * Limits: L * T <= 512.  Launches: a plan upload (per-target offsets carried
- * in kernel parameters, one launch per 512 targets), one init kernel (unless
- * GIVEN) and one persistent kernel, one CTA per target, largest targets
+ * Limits: L * T <= 512.  Launches: a plan upload (per-target offsets and the
+ * work items carried in kernel parameters, one launch per 512 targets and
+ * per 4096 item words), one init kernel (unless GIVEN) and one persistent
+ * kernel: a CTA, or a thread-block cluster of CTAs, per target (small
+ * targets one per CTA of a cluster; see disk_fit_autotune), largest targets
  * first.  Never synchronises, so a call can be captured in a CUDA graph.
  * Scratch:
  * (L+3) canvases of side 2*max((K_b-1)/2, (L+1)*(ceil(s_b)+1))+3 per target
@@ -345,20 +364,23 @@ int disk_fit(const float *d_targets, const int *sizes, int batch, int L, int T,
              float *d_loss_hist, void *stream);
 
 /* Launch-configuration autotuner of disk_fit: times the persistent fit kernel
- * in each built configuration -- 256, 512 or 1024 threads per CTA, and one
- * CTA or a thread-block cluster of 2 or 4 CTAs (on as many SMs) per target --
- * for a few steps each from the radial initialisation on this batch, and
- * records the fastest for every later disk_fit with the same L, T and largest
- * target size (in 32-pixel buckets); without a recorded choice disk_fit uses
- * 512 threads, one CTA per target.  Synchronises the stream (do not call
- * while capturing a graph).  *chosen_config (may be NULL) receives the
- * choice as threads * 16 + CTAs per target. */
+ * in each built configuration -- 256, 512 or 1024 threads per CTA; one CTA
+ * per target, or thread-block clusters of 2, 4 or 8 CTAs (on as many SMs)
+ * in which every target of size >= kbig is split over the whole cluster and
+ * the smaller targets are fitted one per CTA (kbig 0, 65 or 97) -- for a few
+ * steps each from the radial initialisation on this batch, and records the
+ * fastest for every later disk_fit with the same L, T and largest target
+ * size (in 32-pixel buckets); without a recorded choice disk_fit uses 512
+ * threads, one CTA per target.  Synchronises the stream (do not call while
+ * capturing a graph).  *chosen_config (may be NULL) receives the choice as
+ * (kbig << 16) | (threads * 16 + CTAs per cluster). */
 int disk_fit_autotune(const float *d_targets, const int *sizes, int batch, int L,
                       int T, int loss, float eps, int *chosen_config, void *stream);
 
-/* Records a launch configuration (threads * 16 + CTAs per target, one of
- * those disk_fit_autotune tries) for disk_fit calls with this L, T and
- * largest target size kmax.  DISK_ERR_INVALID_ARG for any other value. */
+/* Records a launch configuration ((kbig << 16) | (threads * 16 + CTAs per
+ * cluster), one of those disk_fit_autotune tries) for disk_fit calls with
+ * this L, T and largest target size kmax.  DISK_ERR_INVALID_ARG for any
+ * other value. */
 int disk_fit_set_config(int L, int T, int kmax, int config);
 
 /* One evaluation of the fit objective and its gradient (the hand-written

@@ -11,9 +11,10 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
-#include "sv_layer.cuh"
+#include "sv_pair.cuh"
 
 namespace disk {
 
@@ -87,6 +88,40 @@ LayerGeom layer_geom(const disk_basis *b, int C, int l, bool rot) {
   for (const int hx : {hx16, hx4})
     if (C * (kSvTileW + 2 * hx) / 2 <= 256 && fits(hx)) return {h, hx, 1};
   return {h, h, 0};
+}
+
+// Layer choice code of the first layer of a fused pair (layers l and l + 1 in
+// one launch); the second layer of the pair has code 0.
+constexpr int kSvPairCode = 8;
+
+// Geometry of the fused pair (l, l + 1): halos, staged columns, whether its
+// source (an FP32 intermediate for l > 0) is copied by the tensor-memory
+// accelerator (box of at most 256 elements per dimension), and whether both
+// tap tables are copied into shared memory.  False if it does not fit.
+struct PairGeom {
+  int h0, h1, hxs, tma, taps;
+};
+
+bool pair_geom(const disk_basis *b, int C, int l, PairGeom &pg) {
+  if (l + 1 >= b->L) return false;
+  pg.h0 = halo_of(b->reach[l]);
+  pg.h1 = halo_of(b->reach[l + 1]);
+  const int hs = pg.h0 + pg.h1, hx4 = (hs + 3) & ~3;
+  pg.tma = l > 0 && C * (kSvTileW + 2 * hx4) / 2 <= 256 && kSvPairTileH + 2 * hs <= 256;
+  pg.hxs = pg.tma ? hx4 : hs;
+  const int bt = b->B * b->T;
+  for (const int taps : {1, 0}) {
+    if (sv_pair_geom(pg.h0, pg.h1, pg.hxs, C, bt, taps).total <= (size_t)kSvMaxSmem) {
+      pg.taps = taps;
+      return true;
+    }
+  }
+  return false;
+}
+
+bool fits_pair(const disk_basis *b, int C, int l) {
+  PairGeom pg;
+  return pair_geom(b, C, l, pg);
 }
 
 size_t layer_smem(const disk_basis *b, int C, int l, int pix, bool rot) {
@@ -174,17 +209,51 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "launch rotation_kernel");
   }
-  for (int l = 0; l < L && rc == DISK_OK; ++l) {
+  // Each launch reads the previous launch's output (the caller's image first)
+  // and writes the other intermediate plane (the caller's output last).
+  const void *cur = d_in;
+  for (int l = 0; l < L && rc == DISK_OK;) {
+    const bool pair = !rotated && pix[l] == kSvPairCode && l + 1 < L;
+    const int last = pair ? l + 1 : l;
+    void *dst_ptr = last == L - 1 ? d_out : (cur == bufs[0] ? bufs[1] : bufs[0]);
+    const int src = l == 0 ? user : mid;
+    const int dst = last == L - 1 ? user : mid;
+    const long long spitch = l == 0 ? (long long)in_pitch : mid_pitch;
+    const long long dpitch = last == L - 1 ? (long long)out_pitch : mid_pitch;
+    if (pair) {
+      static thread_local SvPairParams Q;
+      PairGeom pg;
+      if (!pair_geom(b, C, l, pg)) { rc = fail(DISK_ERR_UNSUPPORTED, "fused pair exceeds shared memory"); break; }
+      Q.src = cur; Q.src_pitch = spitch; Q.dst = dst_ptr; Q.dst_pitch = dpitch;
+      Q.maps = d_maps; Q.err = P.err;
+      Q.gtaps0 = layer_taps(b, l, C);
+      Q.gtaps1 = layer_taps(b, l + 1, C);
+      Q.H = H; Q.W = W; Q.C = C; Q.T = b->T;
+      Q.h0 = pg.h0; Q.h1 = pg.h1; Q.hxs = pg.hxs;
+      Q.bt = b->B * b->T;
+      Q.taps_smem = pg.taps;
+      Q.use_tma = 0;
+      std::memcpy(Q.ax, P.ax, sizeof(Q.ax));
+      if (pg.tma && encode) {
+        const int SW = kSvTileW + 2 * pg.hxs, SH = kSvPairTileH + 2 * (pg.h0 + pg.h1);
+        if (encode_rows(encode, &Q.tm, cur, ((long long)C * W + 1) / 2, H, mid_pitch, C * SW / 2, SH))
+          Q.use_tma = 1;
+      }
+      if (!Q.use_tma) Q.hxs = pg.h0 + pg.h1;
+      if (ev) { cudaEventRecord(ev[l], s); cudaEventRecord(ev[l + 1], s); }
+      rc = b->dims == 1 ? launch_sv_pair<1>(src, dst, C, Q, s) : launch_sv_pair<2>(src, dst, C, Q, s);
+      cur = dst_ptr;
+      l += 2;
+      continue;
+    }
     const LayerGeom g = layer_geom(b, C, l, rotated);
     P.halo = g.halo;
     P.halo_x = g.halo_x;
     P.region_w = kSvTileW + 2 * g.halo_x;
-    const int src = l == 0 ? user : mid;
-    const int dst = l == L - 1 ? user : mid;
-    P.src = l == 0 ? d_in : bufs[(l - 1) & 1];
-    P.src_pitch = l == 0 ? (long long)in_pitch : mid_pitch;
-    P.dst = l == L - 1 ? d_out : bufs[l & 1];
-    P.dst_pitch = l == L - 1 ? (long long)out_pitch : mid_pitch;
+    P.src = cur;
+    P.src_pitch = spitch;
+    P.dst = dst_ptr;
+    P.dst_pitch = dpitch;
     P.use_tma = 0;
     if (g.tma && encode) {
       const int RW = P.region_w, RH = sv_tile_h(pix[l]) + 2 * g.halo;
@@ -207,6 +276,8 @@ int run_filter(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_o
     const size_t region = sv_smem_bytes((size_t)P.region_w * (sv_tile_h(pix[l]) + 2 * P.halo), C);
     P.tap_cap = sv_tap_cap(b->dims, b->n_nodes[1], b->B, b->T, region);
     rc = launch_layer(b->dims, rotated, src, dst, C, P, s, pix[l]);
+    cur = dst_ptr;
+    ++l;
   }
   if (ev && rc == DISK_OK) cudaEventRecord(ev[L], s);
   for (int i = 0; i < nbuf; ++i) cudaFreeAsync(bufs[i], s);
@@ -233,8 +304,15 @@ std::vector<int> layer_pix(const disk_basis *b, int H, int W, int C, int dtype, 
     auto it = b->tune_pix.find(tune_key(H, W, C, dtype, rot));
     if (it != b->tune_pix.end() && (int)it->second.size() == b->L) pix = it->second;
   }
-  for (int l = 0; l < b->L; ++l)
-    if (!fits_layer(b, C, l, pix[l], rot)) pix[l] = 2;
+  // a recorded choice that no longer fits falls back to the smaller tile
+  for (int l = 0; l < b->L; ++l) {
+    if (pix[l] == kSvPairCode) {
+      if (!rot && fits_pair(b, C, l) && pix[l + 1] == 0) { ++l; continue; }
+      pix[l] = 2;
+      if (l + 1 < b->L && pix[l + 1] == 0) pix[l + 1] = 2;
+    }
+    if (pix[l] == 0 || !fits_layer(b, C, l, pix[l], rot)) pix[l] = 2;
+  }
   return pix;
 }
 
@@ -262,7 +340,9 @@ int filter_with(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_
 }
 
 // Times both tile configurations layer by layer (CUDA events, three passes
-// each after a warm-up pass) and records the faster one per layer.
+// each after a warm-up pass), then (plain filter) every adjacent pair of
+// layers fused into one launch, and records the fastest cover of the layers
+// by single layers and fused pairs.
 int autotune(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out,
              size_t out_pitch, int H, int W, int C, int dtype, const float *d_maps,
              const float *d_angle, int *chosen, cudaStream_t s) {
@@ -270,13 +350,12 @@ int autotune(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out
   const int L = b->L;
   std::vector<cudaEvent_t> ev(L + 1);
   for (auto &e : ev) DISK_TRY_CUDA(cudaEventCreate(&e), "cudaEventCreate");
-  const int cand[2] = {2, 4};
-  std::vector<float> best_ms(L, 1e30f);
+  std::vector<float> best_ms(L, 1e30f), pair_ms(L, 1e30f);
   std::vector<int> best(L, 2);
   int rc = DISK_OK;
-  for (int c = 0; c < 2 && rc == DISK_OK; ++c) {
-    std::vector<int> pix(L);
-    for (int l = 0; l < L; ++l) pix[l] = fits_layer(b, C, l, cand[c], rot) ? cand[c] : 2;
+  // times the configuration pix: per launch, the time from its first layer's
+  // event to the next launch's
+  auto trial = [&](const std::vector<int> &pix, auto record) {
     rc = filter_with(b, d_in, in_pitch, d_out, out_pitch, H, W, C, dtype, d_maps, d_angle, s,
                      pix.data());
     for (int r = 0; r < 3 && rc == DISK_OK; ++r) {
@@ -284,21 +363,60 @@ int autotune(const disk_basis *b, const void *d_in, size_t in_pitch, void *d_out
                        pix.data(), ev.data());
       cudaError_t e = cudaEventSynchronize(ev[L]);
       if (e != cudaSuccess) { rc = cuda_fail(e, "autotune timing"); break; }
+      record();
+    }
+  };
+  const int cand[2] = {2, 4};
+  for (int c = 0; c < 2 && rc == DISK_OK; ++c) {
+    std::vector<int> pix(L);
+    for (int l = 0; l < L; ++l) pix[l] = fits_layer(b, C, l, cand[c], rot) ? cand[c] : 2;
+    trial(pix, [&] {
       for (int l = 0; l < L; ++l) {
         if (pix[l] != cand[c]) continue;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[l], ev[l + 1]);
         if (ms < best_ms[l]) { best_ms[l] = ms; best[l] = cand[c]; }
       }
-    }
+    });
+  }
+  // fused pairs (l, l + 1), l even in one trial and odd in the other
+  for (int parity = 0; parity < 2 && rc == DISK_OK && !rot; ++parity) {
+    std::vector<int> pix = best;
+    bool any = false;
+    for (int l = parity; l + 1 < L; l += 2)
+      if (fits_pair(b, C, l)) { pix[l] = kSvPairCode; pix[l + 1] = 0; any = true; }
+    if (!any) continue;
+    trial(pix, [&] {
+      for (int l = 0; l + 1 < L; ++l) {
+        if (pix[l] != kSvPairCode) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[l], ev[l + 2]);
+        pair_ms[l] = std::min(pair_ms[l], ms);
+      }
+    });
   }
   for (auto &e : ev) cudaEventDestroy(e);
   if (rc) return rc;
+  // cheapest cover: cost[l] = time of layers l..L-1
+  std::vector<float> cost(L + 1, 0.f);
+  std::vector<int> take_pair(L, 0);
+  for (int l = L - 1; l >= 0; --l) {
+    cost[l] = best_ms[l] + cost[l + 1];
+    if (l + 1 < L && pair_ms[l] < 1e29f && pair_ms[l] + cost[l + 2] < cost[l]) {
+      cost[l] = pair_ms[l] + cost[l + 2];
+      take_pair[l] = 1;
+    }
+  }
+  std::vector<int> pick(L);
+  for (int l = 0; l < L;) {
+    if (take_pair[l]) { pick[l] = kSvPairCode; pick[l + 1] = 0; l += 2; }
+    else { pick[l] = best[l]; ++l; }
+  }
   {
     std::lock_guard<std::mutex> lock(b->tune_mu);
-    b->tune_pix[tune_key(H, W, C, dtype, rot)] = best;
+    b->tune_pix[tune_key(H, W, C, dtype, rot)] = pick;
   }
-  if (chosen) for (int l = 0; l < L; ++l) chosen[l] = best[l];
+  if (chosen) for (int l = 0; l < L; ++l) chosen[l] = pick[l];
   return DISK_OK;
 }
 
@@ -447,6 +565,27 @@ extern "C" int disk_sv_filter_set_tile(const disk_basis *b, int H, int W, int C,
       return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory for this tile");
   std::lock_guard<std::mutex> lock(b->tune_mu);
   b->tune_pix[tune_key(H, W, C, dtype, false)] = std::vector<int>(b->L, pix);
+  return DISK_OK;
+}
+
+extern "C" int disk_sv_filter_set_layers(const disk_basis *b, int H, int W, int C, int dtype,
+                                         const int *choice) {
+  if (!b || !choice) return fail(DISK_ERR_INVALID_ARG, "null basis or choice");
+  std::vector<int> pick(choice, choice + b->L);
+  for (int l = 0; l < b->L; ++l) {
+    if (pick[l] == kSvPairCode) {
+      if (l + 1 >= b->L || pick[l + 1] != 0)
+        return fail(DISK_ERR_INVALID_ARG, "a fused pair needs code 0 on the layer after it");
+      if (!fits_pair(b, C, l)) return fail(DISK_ERR_UNSUPPORTED, "fused pair exceeds shared memory");
+      ++l;
+      continue;
+    }
+    if (pick[l] != 2 && pick[l] != 4) return fail(DISK_ERR_INVALID_ARG, "layer codes are 2, 4, or 8 then 0");
+    if (!fits_layer(b, C, l, pick[l], false))
+      return fail(DISK_ERR_UNSUPPORTED, "layer halo exceeds shared memory for this tile");
+  }
+  std::lock_guard<std::mutex> lock(b->tune_mu);
+  b->tune_pix[tune_key(H, W, C, dtype, false)] = pick;
   return DISK_OK;
 }
 

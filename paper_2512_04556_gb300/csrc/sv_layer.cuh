@@ -395,6 +395,85 @@ __device__ __forceinline__ void sv_tap_column4(const float4 &q00, const float4 &
   }
 }
 
+// The tap loops of one thread's PIX vertically adjacent pixels of one column
+// (cells c, their weights cp, rotations rv, region indexes base; px: the
+// staged region, rows of RW pixels): every tap of the layer, blended per
+// pixel from the node taps, accumulated into acc.  fetch(i): slot i of the
+// layer's node-tap table as a float4; same: the thread's pixels share a cell.
+template <int DIMS, int CH, int PIX, bool ROT, class Fetch>
+__device__ __forceinline__ void sv_run_taps(Fetch fetch, int T, const Cell (&c)[PIX],
+                                            const CellPairs (&cp)[PIX], const float2 (&rv)[PIX],
+                                            const float *px, const int (&base)[PIX], int RW,
+                                            bool same, Acc (&acc)[PIX]) {
+  constexpr int kSvPix = PIX;
+  const int TP = CH == 3 ? (T & ~1) : 0;  // taps taken in pairs
+  // the taps of one pixel group (one cell) from node slot bases b[4]
+  auto pairs = [&](const int (&b)[4], auto column) {
+#pragma unroll 1
+    for (int i = 0; i < TP; i += 2) {
+      float4 A[4];
+      float2 Wt[4];
+      A[0] = fetch(b[0] + i);
+      A[1] = fetch(b[1] + i);
+      // a weight slot holds the pair of its node and of the node next on
+      // axis 0: n10 of an n00, n11 of an n01
+      const float4 w0 = fetch(b[0] + i + 1);
+      Wt[0] = lo2(w0);
+      Wt[1] = hi2(w0);
+      if (DIMS == 2) {
+        A[2] = fetch(b[2] + i);
+        A[3] = fetch(b[3] + i);
+        const float4 w1 = fetch(b[2] + i + 1);
+        Wt[2] = lo2(w1);
+        Wt[3] = hi2(w1);
+      } else {
+        A[2] = A[0]; A[3] = A[1]; Wt[2] = Wt[0]; Wt[3] = Wt[1];
+      }
+      column(A, Wt);
+    }
+  };
+  if (__all_sync(0xffffffffu, same)) {
+    // each thread's pixels share a cell: one node fetch per tap serves them
+    const int b[4] = {c[0].n00 * T, c[0].n10 * T, c[0].n01 * T, c[0].n11 * T};
+    if (CH == 3) {
+      pairs(b, [&](const float4 (&A)[4], const float2 (&Wt)[4]) {
+        sv_pair_column<DIMS, ROT, kSvPix>(A, Wt, cp, rv, px, base[0], RW, acc);
+      });
+    }
+#pragma unroll 2
+    for (int i = TP; i < T; ++i) {
+      const float4 q00 = fetch(b[0] + i), q10 = fetch(b[1] + i);
+      const float4 q01 = DIMS == 2 ? fetch(b[2] + i) : q00;
+      const float4 q11 = DIMS == 2 ? fetch(b[3] + i) : q10;
+      if (CH == 4) {
+        sv_tap_column4<DIMS, ROT, kSvPix>(q00, q10, q01, q11, cp, rv, px, base[0], RW, acc);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kSvPix; ++j)
+          sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rv[j], px, base[j], RW, acc[j]);
+      }
+    }
+  } else {
+    // unrolled so the per-pixel arrays stay in registers
+#pragma unroll
+    for (int j = 0; j < kSvPix; ++j) {
+      const int b[4] = {c[j].n00 * T, c[j].n10 * T, c[j].n01 * T, c[j].n11 * T};
+      if (CH == 3) {
+        pairs(b, [&](const float4 (&A)[4], const float2 (&Wt)[4]) {
+          sv_pair_column<DIMS, ROT, 1>(A, Wt, &cp[j], &rv[j], px, base[j], RW, &acc[j]);
+        });
+      }
+#pragma unroll 1
+      for (int i = TP; i < T; ++i) {
+        const float4 q00 = fetch(b[0] + i), q10 = fetch(b[1] + i);
+        const float4 q01 = DIMS == 2 ? fetch(b[2] + i) : q00;
+        const float4 q11 = DIMS == 2 ? fetch(b[3] + i) : q10;
+        sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rv[j], px, base[j], RW, acc[j]);
+      }
+    }
+  }
+}
+
 template <int DIMS, int SRC, int DST, int CH, int PIX, bool ROT>
 __global__ void __launch_bounds__(kSvThreads, PIX == 2 ? 4 : (CH == 3 ? 2 : 3))
 sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
@@ -568,80 +647,14 @@ sv_layer_kernel(const __grid_constant__ SvLayerParams P) {
   const float *px = s_px;
 
   // The tap loops, once per source of node taps (the choice is uniform over
-  // the block).  fetch(i): slot i of the table as a float4.
-  auto run_taps = [&](auto fetch) {
-    const int TP = CH == 3 ? (T & ~1) : 0;  // taps taken in pairs
-    // the taps of one pixel group (one cell) from node slot bases b[4]
-    auto pairs = [&](const int (&b)[4], auto column) {
-#pragma unroll 1
-      for (int i = 0; i < TP; i += 2) {
-        float4 A[4];
-        float2 Wt[4];
-        A[0] = fetch(b[0] + i);
-        A[1] = fetch(b[1] + i);
-        // a weight slot holds the pair of its node and of the node next on
-        // axis 0: n10 of an n00, n11 of an n01
-        const float4 w0 = fetch(b[0] + i + 1);
-        Wt[0] = lo2(w0);
-        Wt[1] = hi2(w0);
-        if (DIMS == 2) {
-          A[2] = fetch(b[2] + i);
-          A[3] = fetch(b[3] + i);
-          const float4 w1 = fetch(b[2] + i + 1);
-          Wt[2] = lo2(w1);
-          Wt[3] = hi2(w1);
-        } else {
-          A[2] = A[0]; A[3] = A[1]; Wt[2] = Wt[0]; Wt[3] = Wt[1];
-        }
-        column(A, Wt);
-      }
-    };
-    if (__all_sync(0xffffffffu, same)) {
-      // each thread's pixels share a cell: one node fetch per tap serves them
-      const int b[4] = {c[0].n00 * T, c[0].n10 * T, c[0].n01 * T, c[0].n11 * T};
-      if (CH == 3) {
-        pairs(b, [&](const float4 (&A)[4], const float2 (&Wt)[4]) {
-          sv_pair_column<DIMS, ROT, kSvPix>(A, Wt, cp, rv, px, base[0], RW, acc);
-        });
-      }
-#pragma unroll 2
-      for (int i = TP; i < T; ++i) {
-        const float4 q00 = fetch(b[0] + i), q10 = fetch(b[1] + i);
-        const float4 q01 = DIMS == 2 ? fetch(b[2] + i) : q00;
-        const float4 q11 = DIMS == 2 ? fetch(b[3] + i) : q10;
-        if (CH == 4) {
-          sv_tap_column4<DIMS, ROT, kSvPix>(q00, q10, q01, q11, cp, rv, px, base[0], RW, acc);
-        } else {
-#pragma unroll
-          for (int j = 0; j < kSvPix; ++j)
-            sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rv[j], px, base[j], RW, acc[j]);
-        }
-      }
-    } else {
-      // unrolled so the per-pixel arrays stay in registers
-#pragma unroll
-      for (int j = 0; j < kSvPix; ++j) {
-        const int b[4] = {c[j].n00 * T, c[j].n10 * T, c[j].n01 * T, c[j].n11 * T};
-        if (CH == 3) {
-          pairs(b, [&](const float4 (&A)[4], const float2 (&Wt)[4]) {
-            sv_pair_column<DIMS, ROT, 1>(A, Wt, &cp[j], &rv[j], px, base[j], RW, &acc[j]);
-          });
-        }
-#pragma unroll 1
-        for (int i = TP; i < T; ++i) {
-          const float4 q00 = fetch(b[0] + i), q10 = fetch(b[1] + i);
-          const float4 q01 = DIMS == 2 ? fetch(b[2] + i) : q00;
-          const float4 q11 = DIMS == 2 ? fetch(b[3] + i) : q10;
-          sv_tap<DIMS, CH, ROT>(q00, q10, q01, q11, cp[j], rv[j], px, base[j], RW, acc[j]);
-        }
-      }
-    }
-  };
+  // the block).
   if (shared_taps) {
     const float4 *t = s_taps - tap_base;
-    run_taps([&](int idx) { return t[idx]; });
+    sv_run_taps<DIMS, CH, kSvPix, ROT>([&](int idx) { return t[idx]; }, T, c, cp, rv, px, base,
+                                       RW, same, acc);
   } else {
-    run_taps([&](int idx) { return __ldg(P.gtaps + idx); });
+    sv_run_taps<DIMS, CH, kSvPix, ROT>([&](int idx) { return __ldg(P.gtaps + idx); }, T, c, cp,
+                                       rv, px, base, RW, same, acc);
   }
   if (x < P.W) {
 #pragma unroll

@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "disk_fit": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, ctypes.c_float, _i, _i,
                               ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
             "disk_fit_autotune": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _ip, _vp]),
+            "disk_sv_filter_set_layers": (_i, [_vp, _i, _i, _i, _i, _ip]),
             "disk_fit_set_config": (_i, [_i, _i, _i, _i]),
             "disk_mlp_param_count": (ctypes.c_longlong, [_i, _i, _i, _i]),
             "disk_mlp_init": (_i, [_vp, _i, _i, _i, _i, ctypes.c_uint64, _vp]),
@@ -219,6 +220,17 @@ def sv_filter(basis: Basis, img, maps, out=None, stream=None):
         basis.handle, _vp(ip), ipitch, _vp(op), opitch, H, W, C, _dtype_code(img),
         _vp(maps.data_ptr()), _stream(stream)))
     return out
+
+
+def sv_filter_set_layers(basis: Basis, img, choice):
+    """Record every layer's launch choice for this image shape and dtype: 2 or
+    4 pixels per thread, or 8 followed by 0 for a pair of layers fused into
+    one launch."""
+    _, _, H, W, C = _image_args(img)
+    if len(choice) != basis.L:
+        raise ValueError(f"choice needs {basis.L} codes")
+    _check("disk_sv_filter_set_layers", lib().disk_sv_filter_set_layers(
+        basis.handle, H, W, C, _dtype_code(img), _int_arr(list(choice))))
 
 
 def sv_filter_autotune(basis: Basis, img, maps, out=None, stream=None) -> list:
@@ -447,18 +459,23 @@ def fit(packed, sizes, L: int, T: int, steps: int, lr0: float = 1e-3, lr1: float
 def fit_autotune(packed, sizes, L: int, T: int, loss: int = LOSS_MSE, eps: float = 0.0,
                  stream=None) -> tuple:
     """Pick the fit kernel's launch configuration for this batch shape;
-    returns (threads per CTA, CTAs per target)."""
+    returns (threads per CTA, CTAs per cluster, kbig): targets of size >=
+    kbig are split over a whole cluster, smaller ones get one CTA each
+    (kbig = 0: every target split)."""
     out = ctypes.c_int()
     _check("disk_fit_autotune", lib().disk_fit_autotune(
         _vp(packed.data_ptr()), _int_arr(sizes), len(sizes), L, T, loss, eps,
         ctypes.byref(out), _stream(stream)))
-    return out.value // 16, out.value % 16
+    v = out.value
+    return (v & 0xFFFF) // 16, v & 15, v >> 16
 
 
-def fit_set_config(L: int, T: int, kmax: int, threads: int, ctas: int):
-    """Record the fit launch configuration (threads per CTA, CTAs per target)
-    for batches with this L, T and largest target size."""
-    _check("disk_fit_set_config", lib().disk_fit_set_config(L, T, kmax, threads * 16 + ctas))
+def fit_set_config(L: int, T: int, kmax: int, threads: int, ctas: int, kbig: int = 0):
+    """Record the fit launch configuration (threads per CTA, CTAs per cluster,
+    size from which a target is split over the cluster) for batches with this
+    L, T and largest target size."""
+    _check("disk_fit_set_config", lib().disk_fit_set_config(
+        L, T, kmax, (kbig << 16) | (threads * 16 + ctas)))
 
 
 def fit_loss_grad(packed, sizes, theta, loss: int = LOSS_MSE, eps: float = 0.0, stream=None):
