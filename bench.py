@@ -556,7 +556,7 @@ def fit_leg(stream, steps=500, batch=256, reps=3):
     energy = np.array([(t.astype(np.float64) ** 2).sum() for t in tg])
     k2 = np.array([t.shape[0] ** 2 for t in tg], dtype=np.float64)
     L, T = wl.C3["L"], wl.C3["T"]
-    threads, ctas = disk.fit_autotune(packed, sizes, L, T)
+    threads, ctas, kbig = disk.fit_autotune(packed, sizes, L, T)
     theta = torch.zeros((batch, L, T, 3), device="cuda")
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
@@ -585,7 +585,8 @@ def fit_leg(stream, steps=500, batch=256, reps=3):
     return {"fits_per_s": reached / (ms * 1e-3), "unit": "fits/s", "ms_per_batch": ms,
             "batch": batch, "steps": steps, "reached_tau": reached, "tau_rel_mse": tau,
             "median_rel_mse": float(np.median(rel)), "init": "sparse sampling",
-            "cuda_graph": True, "cta_threads": threads, "ctas_per_target": ctas,
+            "cuda_graph": True, "cta_threads": threads, "ctas_per_cluster": ctas,
+            "split_from_size": kbig if ctas > 1 else None,
             "targets": "seeded polygons, rings, 5-8 point stars, annuli; odd sizes 33..129"}
 
 

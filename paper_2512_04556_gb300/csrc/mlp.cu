@@ -9,7 +9,9 @@
 // hidden layers ReLU, output linear.  Matrix products run in a tiled FP32
 // SIMT GEMM (64 x 64 tile, 16-deep K slices in shared memory, 4 x 4 outputs
 // per thread) whose epilogue adds the bias, applies ReLU, or multiplies by
-// the ReLU mask of the backward pass.
+// the ReLU mask of the backward pass; products whose tile grid cannot fill
+// the GPU split K and sum the slices (in a fixed order) before the epilogue.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -28,13 +30,17 @@ template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(kGemmThreads)
 gemm_kernel(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C, int M,
             int N, int K, int lda, int ldb, int ldc, const float *__restrict__ bias,
-            const float *__restrict__ mask, int ldm) {
+            const float *__restrict__ mask, int ldm, int kchunk, long long cz) {
   __shared__ float As[kBK][kBM + 4];
   __shared__ float Bs[kBK][kBN + 4];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  // split-K: blockIdx.z takes k in [kb, K') and writes its own slice of C
+  const int kb = blockIdx.z * kchunk;
+  K = min(K, kb + kchunk);
+  C += blockIdx.z * cz;
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += kBK) {
+  for (int k0 = kb; k0 < K; k0 += kBK) {
     for (int e = tid; e < kBM * kBK; e += kGemmThreads) {
       int mm, kk;
       if (TA) { mm = e % kBM; kk = e / kBM; } else { kk = e % kBK; mm = e / kBK; }
@@ -83,12 +89,55 @@ gemm_kernel(const float *__restrict__ A, const float *__restrict__ B, float *__r
   }
 }
 
+// Sum of the split-K slices ws[z][m][n] in slice order, then the epilogue.
+template <int EPI>
+__global__ void splitk_reduce_kernel(const float *__restrict__ ws, int splits, int M, int N,
+                                     float *__restrict__ C, int ldc, const float *__restrict__ bias,
+                                     const float *__restrict__ mask, int ldm) {
+  const long long MN = (long long)M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < MN;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / N), n = (int)(i % N);
+    float v = 0.f;
+    for (int z = 0; z < splits; ++z) v += ws[z * MN + i];
+    if (EPI == EPI_BIAS_RELU) v = fmaxf(v + bias[n], 0.f);
+    if (EPI == EPI_BIAS) v += bias[n];
+    if (EPI == EPI_RELU_MASK) v = mask[(long long)m * ldm + n] > 0.f ? v : 0.f;
+    C[(long long)m * ldc + n] = v;
+  }
+}
+
+constexpr int kGemmFillCtas = 2 * 152;  // about two waves of CTAs over the SMs
+
 template <bool TA, bool TB, int EPI>
 int gemm(const float *A, const float *B, float *C, int M, int N, int K, int lda, int ldb, int ldc,
          const float *bias, const float *mask, int ldm, cudaStream_t s) {
   dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
-  gemm_kernel<TA, TB, EPI><<<grid, kGemmThreads, 0, s>>>(A, B, C, M, N, K, lda, ldb, ldc, bias, mask, ldm);
-  DISK_TRY_CUDA(cudaGetLastError(), "launch gemm_kernel");
+  // a tile grid too small to fill the GPU splits K (slices of >= 128) and
+  // sums the slices in a second pass
+  int splits = 1;
+  while ((long long)grid.x * grid.y * splits < kGemmFillCtas && K / (2 * splits) >= 128) splits *= 2;
+  if (splits == 1) {
+    gemm_kernel<TA, TB, EPI><<<grid, kGemmThreads, 0, s>>>(A, B, C, M, N, K, lda, ldb, ldc, bias,
+                                                           mask, ldm, K, 0);
+    DISK_TRY_CUDA(cudaGetLastError(), "launch gemm_kernel");
+    return DISK_OK;
+  }
+  const int kchunk = ((K + splits - 1) / splits + kBK - 1) / kBK * kBK;
+  const long long MN = (long long)M * N;
+  float *ws = nullptr;
+  DISK_TRY_CUDA(scratch_alloc(&ws, (size_t)splits * MN * sizeof(float), s), "scratch_alloc(split-K)");
+  grid.z = splits;
+  gemm_kernel<TA, TB, EPI_NONE><<<grid, kGemmThreads, 0, s>>>(A, B, ws, M, N, K, lda, ldb, N,
+                                                              nullptr, nullptr, 0, kchunk, MN);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    const int blocks = (int)std::min<long long>((MN + 255) / 256, 152LL * 8);
+    splitk_reduce_kernel<EPI><<<blocks, 256, 0, s>>>(ws, splits, M, N, C, ldc, bias, mask, ldm);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(ws, s);
+  if (e != cudaSuccess) return cuda_fail(e, "launch split-K gemm");
   return DISK_OK;
 }
 

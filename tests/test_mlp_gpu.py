@@ -63,19 +63,20 @@ def test_learned_initializer_gains_over_the_radial_start(torch_cuda, capsys):
     torch = torch_cuda
     from paper_2512_04556_gb300 import disk, learned_init as li
     L, T, steps = 3, 8, 200
-    train_t = wl.shape_batch(3000, kmin=17, kmax=33, first=0)
+    train_t = wl.shape_batch(8000, kmin=17, kmax=33, first=0)
     held_t = wl.shape_batch(128, kmin=17, kmax=33, first=5_000_000)
     th, _ = li.fit_pairs(train_t, L, T, steps)
     X = li.features(train_t)
     Y = li.to_labels(th, [t.shape[0] for t in train_t], T)
-    net = disk.MLP(li.SIDE * li.SIDE, 256, 2, L * T * 3, seed=1)
-    li.train(net, X, Y, epochs=20, batch=128)
+    net = disk.MLP(li.SIDE * li.SIDE, 512, 2, L * T * 3, seed=1)
+    li.train(net, X, Y, epochs=30, batch=128)
     res = li.evaluate(net, held_t, L, T, steps)
     with capsys.disabled():
         print("\nlearned-init gain (toy config):", res)
-    # this toy configuration (3,000 pairs, L = 3, T = 8, 200 steps) gains
-    # about 1.45x; the floor is 1.25x fewer steps
-    assert res["speedup"] >= 1.25, res
+    # this small configuration (8,000 pairs of 17..33 px targets, L = 3,
+    # T = 8, 200 steps, a 4096-512-512-72 network) gains about 3.8x on
+    # GB300; the floor is 2.5x fewer steps
+    assert res["speedup"] >= 2.5, res
     assert res["median_start_loss_ratio"] < 1.0, res
 
 
