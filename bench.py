@@ -43,7 +43,8 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) of one pass (the L sv_layer launches) from an
 # ncu capture, tagged with the hash of the filter kernel's sources at the
 # capture; reported as null once the sources differ.
-TRAFFIC_PER_PASS = {"bytes": None, "sources_sha16": None, "capture": None}
+TRAFFIC_PER_PASS = {"bytes": 846.8e6, "sources_sha16": "4c3e2f069232799a",
+                    "capture": "profiles/sv_layer_4k_fp16_2d.md"}
 KERNEL_SOURCES = ("sv_layer.cuh", "sv_common.cuh", "sv_layer_2d.cu", "sv_filter.cu")
 
 
@@ -71,6 +72,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="disk", choices=["disk", "reference"])
     p.add_argument("--no-extras", action="store_true", help="skip dense/e2e/cpu extras")
+    p.add_argument("--layers", default=None,
+                   help="per-layer launch codes (e.g. 2,2,2,4) instead of the autotuner's "
+                        "choice; for profilers, whose per-launch overhead distorts its timings")
     return p.parse_args()
 
 
@@ -173,7 +177,11 @@ def run_disk(args, rank, world, dist):
         disk.sv_filter(basis, d_img, d_maps, out=d_out, stream=stream)
 
     # tile configuration picked by the library's autotuner for this frame shape
-    tile_pix = disk.sv_filter_autotune(basis, d_img, d_maps, out=d_out, stream=stream)
+    if args.layers:
+        tile_pix = [int(v) for v in args.layers.split(",")]
+        disk.sv_filter_set_layers(basis, d_img, tile_pix)
+    else:
+        tile_pix = disk.sv_filter_autotune(basis, d_img, d_maps, out=d_out, stream=stream)
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -199,12 +207,20 @@ def run_disk(args, rank, world, dist):
     px = H * W
     value = world * px / (ms * 1e-3) / 1e9
     res = {"ms_per_step": ms, "value": value, "clocks": clk.summary(), "wall_s": wall,
-           "tile": "per layer (autotuned): " + ", ".join(f"32x{8 * p}" for p in tile_pix),
+           "tile": ("per layer (given): " if args.layers else "per layer (autotuned): ")
+                   + ", ".join(tile_name(p) for p in tile_pix),
            "gpu_launches": K * basis.L, "step_ms_min": float(np.min(step_ms)),
            "step_ms_median": float(np.median(step_ms))}
     if rank == 0 and not args.no_extras:
         res.update(extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream))
     return res
+
+
+def tile_name(code: int) -> str:
+    """A layer's launch code: 2 or 4 pixels per thread (32 x 16 or 32 x 32
+    tiles), 8 for the first layer of a fused pair (32 x 16 output tiles), 0
+    for the second."""
+    return {8: "fused pair 32x16", 0: "(in pair)"}.get(code, f"32x{8 * code}")
 
 
 def extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream):
@@ -402,7 +418,7 @@ def bokeh1080_leg(flush, stream):
     mse = float(((out - dense) ** 2).mean().item())
     px = H * W
     return {"value": px / (ms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": ms,
-            "L": b.L, "T": b.T, "tile": ", ".join(f"32x{8 * p}" for p in tiles),
+            "L": b.L, "T": b.T, "tile": ", ".join(tile_name(p) for p in tiles),
             "dense_ms": dms, "dense_kernel": f"{c['dense_K']}x{c['dense_K']}, 16 disks",
             "speedup_disk_vs_dense": dms / ms,
             "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20)))}
@@ -487,7 +503,7 @@ def gaussian_leg(d_img, flush, stream):
     mse_g = float(((d_g.float() - d_dense.float()) ** 2).mean().item())
     return {"value": px / (ms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": ms,
             "L": b.L, "T": b.T, "nodes": "11 Gaussians, sigma 1..11 px",
-            "map": "tilt-shift, sigma 1..11", "tile": ", ".join(f"32x{8 * p}" for p in tiles),
+            "map": "tilt-shift, sigma 1..11", "tile": ", ".join(tile_name(p) for p in tiles),
             "dense_ms": dms, "dense_kernel": f"{g['dense_K']}x{g['dense_K']}, 41 LUT nodes",
             "speedup_disk_vs_dense": dms / ms,
             "psnr_disk_vs_dense_db": float(10 * np.log10(1.0 / max(mse, 1e-20))),
@@ -532,7 +548,7 @@ def rotated_leg(preset, basis_file, tangential, d_img, flush, stream):
     mse = float(((d_out.float() - d_dense.float()) ** 2).mean().item())
     return {"value": px / (ms * 1e-3) / 1e9, "unit": "Gpix/s", "ms_per_step": ms,
             "L": b.L, "T": b.T, "nodes": f"{b.n_nodes[0]} along the strength axis, turned per pixel",
-            "tile": ", ".join(f"32x{8 * p}" for p in tiles),
+            "tile": ", ".join(tile_name(p) for p in tiles),
             "unrotated_ms": pms, "rotation_overhead": ms / pms - 1.0,
             "dense_ms": dms, "dense_kernel": f"{K}x{K}, 16 strengths x {len(a_nodes)} angles",
             "speedup_disk_vs_dense": dms / ms,
@@ -556,7 +572,7 @@ def fit_leg(stream, steps=500, batch=256, reps=3):
     energy = np.array([(t.astype(np.float64) ** 2).sum() for t in tg])
     k2 = np.array([t.shape[0] ** 2 for t in tg], dtype=np.float64)
     L, T = wl.C3["L"], wl.C3["T"]
-    threads, ctas, kbig = disk.fit_autotune(packed, sizes, L, T)
+    threads, ctas = disk.fit_autotune(packed, sizes, L, T)
     theta = torch.zeros((batch, L, T, 3), device="cuda")
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
@@ -585,8 +601,7 @@ def fit_leg(stream, steps=500, batch=256, reps=3):
     return {"fits_per_s": reached / (ms * 1e-3), "unit": "fits/s", "ms_per_batch": ms,
             "batch": batch, "steps": steps, "reached_tau": reached, "tau_rel_mse": tau,
             "median_rel_mse": float(np.median(rel)), "init": "sparse sampling",
-            "cuda_graph": True, "cta_threads": threads, "ctas_per_cluster": ctas,
-            "split_from_size": kbig if ctas > 1 else None,
+            "cuda_graph": True, "cta_threads": threads, "ctas_per_target": ctas,
             "targets": "seeded polygons, rings, 5-8 point stars, annuli; odd sizes 33..129"}
 
 
@@ -660,6 +675,41 @@ def cpu_baseline(sample_px=(256, 256), budget_s=15.0):
             "sample": f"{n} x centre crop {h}x{w} of the 3840x2160 frame, FP64, {dt:.1f} s"}
 
 
+def oracle_full_frames():
+    """The FP64 oracle on the whole 256 x 256 FP32 frame (random 4-node basis,
+    L=3, T=8) and the whole 1920 x 1080 FP32 frame (16 fitted disks, L=4,
+    T=16), one pass each on the host cores; the 4K frame is timed on a
+    512 x 512 centre crop and extrapolated per pixel."""
+    import oracle
+    from oracle import basis_io
+    out = {"cores": oracle.num_threads(), "kind": "oracle"}
+    img, maps, n_nodes, nodes, theta = wl.c1_inputs()
+    t0 = time.perf_counter()
+    oracle.sv_filter(img.astype(np.float64), maps.astype(np.float64), n_nodes,
+                     np.asarray(nodes, np.float64), theta.astype(np.float64))
+    dt = time.perf_counter() - t0
+    out["sv_256_fp32"] = {"s": dt, "gpix_per_s": 256 * 256 / dt / 1e9, "frame": "full 256x256"}
+    c = wl.C2
+    img2 = wl.image_rects(c["H"], c["W"], 3).astype(np.float64)
+    m2 = wl.param_map(c["H"], c["W"], *c["map_range"], sigma=c["map_sigma"])[None].astype(np.float64)
+    axes, th = basis_io.read(os.path.join(BASES, "disk16_L4T16.dkb"))
+    t0 = time.perf_counter()
+    oracle.sv_filter(img2, m2, [len(a) for a in axes], np.concatenate(axes).astype(np.float64),
+                     th.astype(np.float64))
+    dt = time.perf_counter() - t0
+    out["sv_1080p_fp32"] = {"s": dt, "gpix_per_s": c["H"] * c["W"] / dt / 1e9,
+                            "frame": "full 1920x1080"}
+    crop = _oracle_crop(512, 512)
+    t0 = time.perf_counter()
+    oracle.sv_filter(*crop)
+    dt = time.perf_counter() - t0
+    H, W = wl.C4["H"], wl.C4["W"]
+    out["sv_4k_fp16_2d"] = {"s_per_frame_extrapolated": dt * H * W / (512 * 512),
+                            "gpix_per_s": 512 * 512 / dt / 1e9,
+                            "frame": "512x512 centre crop, extrapolated per pixel"}
+    return out
+
+
 def run_reference(args, base):
     """Reference arm: the oracle on the host cores, one 128 x 128 centre crop
     of the frame per step."""
@@ -717,6 +767,7 @@ def main():
         if not args.no_extras and world == 1:
             line["cpu_baseline"] = cpu_baseline()
             line["fit"]["cpu_baseline"] = fit_cpu_baseline()
+            line["oracle_full_frames"] = oracle_full_frames()
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

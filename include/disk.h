@@ -346,11 +346,9 @@ int disk_synth_kernel(const float *d_theta, int batch, int L, int T, int K,
  * d_final_loss: float [batch], loss at the result (may be NULL).
  * d_loss_hist: float [batch][steps+1], loss before every step and after the
  *   last (may be NULL).
- * Limits: L * T <= 512.  Launches: a plan upload (per-target offsets and the
- * work items carried in kernel parameters, one launch per 512 targets and
- * per 4096 item words), one init kernel (unless GIVEN) and one persistent
- * kernel: a CTA, or a thread-block cluster of CTAs, per target (small
- * targets one per CTA of a cluster; see disk_fit_autotune), largest targets
+ * Limits: L * T <= 512.  Launches: a plan upload (per-target offsets carried
+ * in kernel parameters, one launch per 512 targets), one init kernel (unless
+ * GIVEN) and one persistent kernel, one CTA per target, largest targets
  * first.  Never synchronises, so a call can be captured in a CUDA graph.
  * Scratch:
  * (L+3) canvases of side 2*max((K_b-1)/2, (L+1)*(ceil(s_b)+1))+3 per target
@@ -364,23 +362,20 @@ int disk_fit(const float *d_targets, const int *sizes, int batch, int L, int T,
              float *d_loss_hist, void *stream);
 
 /* Launch-configuration autotuner of disk_fit: times the persistent fit kernel
- * in each built configuration -- 256, 512 or 1024 threads per CTA; one CTA
- * per target, or thread-block clusters of 2, 4 or 8 CTAs (on as many SMs)
- * in which every target of size >= kbig is split over the whole cluster and
- * the smaller targets are fitted one per CTA (kbig 0, 65 or 97) -- for a few
- * steps each from the radial initialisation on this batch, and records the
- * fastest for every later disk_fit with the same L, T and largest target
- * size (in 32-pixel buckets); without a recorded choice disk_fit uses 512
- * threads, one CTA per target.  Synchronises the stream (do not call while
- * capturing a graph).  *chosen_config (may be NULL) receives the choice as
- * (kbig << 16) | (threads * 16 + CTAs per cluster). */
+ * in each built configuration -- 256, 512 or 1024 threads per CTA, and one
+ * CTA or a thread-block cluster of 2 or 4 CTAs (on as many SMs) per target --
+ * for a few steps each from the radial initialisation on this batch, and
+ * records the fastest for every later disk_fit with the same L, T and largest
+ * target size (in 32-pixel buckets); without a recorded choice disk_fit uses
+ * 512 threads, one CTA per target.  Synchronises the stream (do not call
+ * while capturing a graph).  *chosen_config (may be NULL) receives the
+ * choice as threads * 16 + CTAs per target. */
 int disk_fit_autotune(const float *d_targets, const int *sizes, int batch, int L,
                       int T, int loss, float eps, int *chosen_config, void *stream);
 
-/* Records a launch configuration ((kbig << 16) | (threads * 16 + CTAs per
- * cluster), one of those disk_fit_autotune tries) for disk_fit calls with
- * this L, T and largest target size kmax.  DISK_ERR_INVALID_ARG for any
- * other value. */
+/* Records a launch configuration (threads * 16 + CTAs per target, one of
+ * those disk_fit_autotune tries) for disk_fit calls with this L, T and
+ * largest target size kmax.  DISK_ERR_INVALID_ARG for any other value. */
 int disk_fit_set_config(int L, int T, int kmax, int config);
 
 /* One evaluation of the fit objective and its gradient (the hand-written

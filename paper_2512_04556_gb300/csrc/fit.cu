@@ -41,7 +41,7 @@ namespace {
 constexpr int kFitThreads = 512;      // init kernel and default fit CTA size
 constexpr int kFitWarps = kFitThreads / 32;
 constexpr int kFitMaxWarps = 32;      // largest fit CTA: 1024 threads
-constexpr int kFitMaxCluster = 8;     // CTAs per thread-block cluster
+constexpr int kFitMaxCluster = 4;     // CTAs per target
 
 struct FitMeta {
   long long tgt_off;     // floats into the packed targets
@@ -54,11 +54,7 @@ struct FitMeta {
 struct FitArgs {
   const float *targets;
   const FitMeta *meta;
-  // work items, one per cluster (item_stride ints each): a flag (1 = one
-  // target over all the cluster's CTAs, 0 = one target per CTA), then the
-  // target of each CTA (-1: none); largest work first
-  const int *items;
-  int item_stride;
+  const int *order;
   float *scratch;
   int *idx_scratch;
   float *theta;          // [batch][L][T][3], pixels
@@ -427,10 +423,11 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
   __syncthreads();  // sh.g complete for the update
 }
 
-// All steps of the fit of target b by the CL CTAs that share it (CL = 1: this
-// CTA alone; rank: this CTA's index among them).
-template <int CL>
-__device__ void fit_target(FitShared &sh, const FitArgs &A, int b, unsigned rank) {
+template <int NT, int CL>
+__global__ void __launch_bounds__(NT) fit_kernel(FitArgs A) {
+  __shared__ FitShared sh;
+  const unsigned rank = target_rank<CL>();
+  const int b = A.order[blockIdx.x / CL];
   const FitMeta m = A.meta[b];
   const int L = A.L, T = A.T, P = L * T * 3, N = 2 * m.R + 1;
   const size_t plane = (size_t)N * N;
@@ -494,45 +491,21 @@ __device__ void fit_target(FitShared &sh, const FitArgs &A, int b, unsigned rank
   target_sync<CL>();  // no CTA leaves while another may read its shared memory
 }
 
-// One work item per cluster of CL CTAs (CL = 1: per CTA): a large target
-// split over the cluster, or up to CL small targets fitted independently,
-// one per CTA, with block barriers only.
-// At most 64 registers per thread: 1024 threads' worth of CTAs per SM at
-// any CTA size.
-template <int NT, int CL>
-__global__ void __launch_bounds__(NT, 1024 / NT) fit_kernel(FitArgs A) {
-  __shared__ FitShared sh;
-  const unsigned rank = target_rank<CL>();
-  const int *item = A.items + (size_t)(blockIdx.x / CL) * A.item_stride;
-  if (CL > 1 && item[0]) {
-    fit_target<CL>(sh, A, item[1], rank);
-  } else {
-    const int b = item[1 + rank];
-    if (b >= 0) fit_target<1>(sh, A, b, 0);
-  }
-}
-
 // ---- host side -----------------------------------------------------------------
 
-constexpr int kPlanChunk = 512;   // 512 * 40 bytes of metadata per upload launch
-constexpr int kItemChunk = 4096;  // 16 KB of work-item words per upload launch
+constexpr int kPlanChunk = 512;  // 512 * (40 + 4) bytes: inside the parameter limit
 
 struct PlanChunk {
   int first, count;
   FitMeta meta[kPlanChunk];
+  int order[kPlanChunk];
 };
 
-struct ItemChunk {
-  int first, count;
-  int words[kItemChunk];
-};
-
-__global__ void plan_upload_kernel(const __grid_constant__ PlanChunk c, FitMeta *meta) {
-  for (int j = threadIdx.x; j < c.count; j += blockDim.x) meta[c.first + j] = c.meta[j];
-}
-
-__global__ void item_upload_kernel(const __grid_constant__ ItemChunk c, int *items) {
-  for (int j = threadIdx.x; j < c.count; j += blockDim.x) items[c.first + j] = c.words[j];
+__global__ void plan_upload_kernel(const __grid_constant__ PlanChunk c, FitMeta *meta, int *order) {
+  for (int j = threadIdx.x; j < c.count; j += blockDim.x) {
+    meta[c.first + j] = c.meta[j];
+    order[c.first + j] = c.order[j];
+  }
 }
 
 struct FitPlan {
@@ -574,28 +547,6 @@ int plan_fit(const int *sizes, int batch, int L, FitPlan &plan) {
   return DISK_OK;
 }
 
-// Work items for clusters of CL CTAs (stride CL + 1 ints each): every target
-// of size >= kbig alone on a whole cluster (largest first), then the other
-// targets CL at a time, one per CTA, in decreasing size.  CL = 1: one
-// target per CTA.
-std::vector<int> make_items(const FitPlan &plan, int CL, int kbig) {
-  std::vector<int> items, small;
-  for (int b : plan.order) {
-    if (CL > 1 && plan.meta[b].K >= kbig) {
-      items.push_back(1);
-      items.push_back(b);
-      for (int r = 1; r < CL; ++r) items.push_back(-1);
-    } else {
-      small.push_back(b);
-    }
-  }
-  for (size_t i = 0; i < small.size(); i += CL) {
-    items.push_back(0);
-    for (int r = 0; r < CL; ++r) items.push_back(i + r < small.size() ? small[i + r] : -1);
-  }
-  return items;
-}
-
 // ---- launch-configuration autotuner ----------------------------------------------
 // The launch configuration -- threads per CTA (256, 512, 1024) and CTAs per
 // target (1, 2 or 4, a thread-block cluster) -- trades the parallelism of one
@@ -606,10 +557,7 @@ std::vector<int> make_items(const FitPlan &plan, int CL, int kbig) {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, int> g_tune;
 
-// A launch configuration is encoded as (kbig << 16) | (threads * 16 + CTAs
-// per cluster): with clusters of 2..8 CTAs, targets of size >= kbig are
-// split over a whole cluster and smaller ones get one CTA each (kbig = 0:
-// every target split).
+// A launch configuration is encoded as threads * 16 + CTAs per target.
 int tuned_config(int L, int T, int kmax) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto it = g_tune.find(std::make_tuple(L, T, (kmax + 31) / 32));
@@ -617,13 +565,13 @@ int tuned_config(int L, int T, int kmax) {
 }
 
 template <int NT, int CL>
-cudaError_t launch_fit(const FitArgs &A, int clusters, cudaStream_t s) {
+cudaError_t launch_fit(const FitArgs &A, cudaStream_t s) {
   if (CL == 1) {
-    fit_kernel<NT, 1><<<clusters, NT, 0, s>>>(A);
+    fit_kernel<NT, 1><<<A.batch, NT, 0, s>>>(A);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(clusters * CL);
+  cfg.gridDim = dim3(A.batch * CL);
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
@@ -637,27 +585,20 @@ cudaError_t launch_fit(const FitArgs &A, int clusters, cudaStream_t s) {
   return cudaLaunchKernelEx(&cfg, fit_kernel<NT, CL>, A);
 }
 
-cudaError_t launch_fit_config(int config, const FitArgs &A, int clusters, cudaStream_t s) {
-  switch (config & 0xFFFF) {
-    case 256 * 16 + 1: return launch_fit<256, 1>(A, clusters, s);
-    case 1024 * 16 + 1: return launch_fit<1024, 1>(A, clusters, s);
-    case 512 * 16 + 2: return launch_fit<512, 2>(A, clusters, s);
-    case 1024 * 16 + 2: return launch_fit<1024, 2>(A, clusters, s);
-    case 512 * 16 + 4: return launch_fit<512, 4>(A, clusters, s);
-    case 1024 * 16 + 4: return launch_fit<1024, 4>(A, clusters, s);
-    case 512 * 16 + 8: return launch_fit<512, 8>(A, clusters, s);
-    case 1024 * 16 + 8: return launch_fit<1024, 8>(A, clusters, s);
-    default: return launch_fit<512, 1>(A, clusters, s);
+cudaError_t launch_fit_config(int config, const FitArgs &A, cudaStream_t s) {
+  switch (config) {
+    case 256 * 16 + 1: return launch_fit<256, 1>(A, s);
+    case 1024 * 16 + 1: return launch_fit<1024, 1>(A, s);
+    case 512 * 16 + 2: return launch_fit<512, 2>(A, s);
+    case 1024 * 16 + 2: return launch_fit<1024, 2>(A, s);
+    case 512 * 16 + 4: return launch_fit<512, 4>(A, s);
+    case 1024 * 16 + 4: return launch_fit<1024, 4>(A, s);
+    default: return launch_fit<512, 1>(A, s);
   }
 }
 
-constexpr int kFitConfigs[] = {
-    256 * 16 + 1, 512 * 16 + 1, 1024 * 16 + 1,
-    512 * 16 + 2, 1024 * 16 + 2, (97 << 16) | (512 * 16 + 2), (97 << 16) | (1024 * 16 + 2),
-    512 * 16 + 4, 1024 * 16 + 4, (65 << 16) | (512 * 16 + 4), (97 << 16) | (512 * 16 + 4),
-    (65 << 16) | (1024 * 16 + 4), (97 << 16) | (1024 * 16 + 4),
-    (65 << 16) | (512 * 16 + 8), (97 << 16) | (512 * 16 + 8),
-    (65 << 16) | (1024 * 16 + 8), (97 << 16) | (1024 * 16 + 8)};
+constexpr int kFitConfigs[] = {256 * 16 + 1, 512 * 16 + 1, 1024 * 16 + 1, 512 * 16 + 2,
+                               1024 * 16 + 2, 512 * 16 + 4, 1024 * 16 + 4};
 
 int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, int steps,
             float lr0, float lr1, int init, int loss, float eps, unsigned long long seed,
@@ -675,13 +616,9 @@ int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, i
   FitPlan plan;
   int rc = plan_fit(sizes, batch, L, plan);
   if (rc) return rc;
-  const int cfg = config > 0 ? config : tuned_config(L, T, plan.kmax);
-  const int CL = cfg & 15;
-  const std::vector<int> items = make_items(plan, CL, cfg >> 16);
-  const int clusters = (int)(items.size() / (CL + 1));
   const size_t meta_bytes = plan.meta.size() * sizeof(FitMeta);
-  const size_t item_bytes = items.size() * sizeof(int);
-  const size_t head = ((meta_bytes + item_bytes + 255) / 256) * 256;
+  const size_t order_bytes = plan.order.size() * sizeof(int);
+  const size_t head = ((meta_bytes + order_bytes + 255) / 256) * 256;
   const size_t bytes = head + plan.scratch_floats * sizeof(float) + plan.idx_ints * sizeof(int);
   char *buf = nullptr;
   DISK_TRY_CUDA(scratch_alloc(reinterpret_cast<void **>(&buf), bytes, s), "scratch_alloc(fit scratch)");
@@ -692,16 +629,12 @@ int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, i
     static thread_local PlanChunk chunk;
     chunk.first = first;
     chunk.count = std::min(kPlanChunk, batch - first);
-    for (int j = 0; j < chunk.count; ++j) chunk.meta[j] = plan.meta[first + j];
-    plan_upload_kernel<<<1, 256, 0, s>>>(chunk, reinterpret_cast<FitMeta *>(buf));
-    e = cudaGetLastError();
-  }
-  for (int first = 0; first < (int)items.size() && e == cudaSuccess; first += kItemChunk) {
-    static thread_local ItemChunk chunk;
-    chunk.first = first;
-    chunk.count = std::min(kItemChunk, (int)items.size() - first);
-    for (int j = 0; j < chunk.count; ++j) chunk.words[j] = items[first + j];
-    item_upload_kernel<<<1, 256, 0, s>>>(chunk, reinterpret_cast<int *>(buf + meta_bytes));
+    for (int j = 0; j < chunk.count; ++j) {
+      chunk.meta[j] = plan.meta[first + j];
+      chunk.order[j] = plan.order[first + j];
+    }
+    plan_upload_kernel<<<1, 256, 0, s>>>(chunk, reinterpret_cast<FitMeta *>(buf),
+                                         reinterpret_cast<int *>(buf + meta_bytes));
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
@@ -711,8 +644,7 @@ int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, i
   FitArgs A;
   A.targets = d_targets;
   A.meta = reinterpret_cast<const FitMeta *>(buf);
-  A.items = reinterpret_cast<const int *>(buf + meta_bytes);
-  A.item_stride = CL + 1;
+  A.order = reinterpret_cast<const int *>(buf + meta_bytes);
   A.scratch = reinterpret_cast<float *>(buf + head);
   A.idx_scratch = reinterpret_cast<int *>(buf + head + plan.scratch_floats * sizeof(float));
   A.theta = d_theta;
@@ -723,7 +655,9 @@ int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, i
   A.eps = eps; A.lr0 = lr0; A.lr1 = lr1;
   if (mode == 0 && init != 0) fit_init_kernel<<<batch, kFitThreads, 0, s>>>(A, init, seed);
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_fit_config(cfg, A, clusters, s);
+  if (e == cudaSuccess) {
+    e = launch_fit_config(config > 0 ? config : tuned_config(L, T, plan.kmax), A, s);
+  }
   cudaFreeAsync(buf, s);
   if (e != cudaSuccess) return cuda_fail(e, "launch fit kernels");
   return DISK_OK;

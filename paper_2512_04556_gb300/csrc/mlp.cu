@@ -11,11 +11,15 @@
 // per thread) whose epilogue adds the bias, applies ReLU, or multiplies by
 // the ReLU mask of the backward pass; products whose tile grid cannot fill
 // the GPU split K and sum the slices (in a fixed order) before the epilogue.
+// Products of 2^24 multiply-adds and more (all of the benchmark network's)
+// run on the tensor cores instead (tc_gemm.cuh: four TF32 products, FP32
+// accuracy) with the same split-K reduction and epilogue.
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "internal.h"
+#include "tc_gemm.cuh"
 
 namespace disk {
 namespace {
@@ -89,17 +93,20 @@ gemm_kernel(const float *__restrict__ A, const float *__restrict__ B, float *__r
   }
 }
 
-// Sum of the split-K slices ws[z][m][n] in slice order, then the epilogue.
+// Sum of the split-K slices ws[z * zs + m * ldw + n] in slice order, then
+// the epilogue.
 template <int EPI>
-__global__ void splitk_reduce_kernel(const float *__restrict__ ws, int splits, int M, int N,
-                                     float *__restrict__ C, int ldc, const float *__restrict__ bias,
+__global__ void splitk_reduce_kernel(const float *__restrict__ ws, int splits, long long zs,
+                                     int ldw, int M, int N, float *__restrict__ C, int ldc,
+                                     const float *__restrict__ bias,
                                      const float *__restrict__ mask, int ldm) {
   const long long MN = (long long)M * N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < MN;
        i += (long long)gridDim.x * blockDim.x) {
     const int m = (int)(i / N), n = (int)(i % N);
+    const long long w = (long long)m * ldw + n;
     float v = 0.f;
-    for (int z = 0; z < splits; ++z) v += ws[z * MN + i];
+    for (int z = 0; z < splits; ++z) v += ws[z * zs + w];
     if (EPI == EPI_BIAS_RELU) v = fmaxf(v + bias[n], 0.f);
     if (EPI == EPI_BIAS) v += bias[n];
     if (EPI == EPI_RELU_MASK) v = mask[(long long)m * ldm + n] > 0.f ? v : 0.f;
@@ -109,9 +116,26 @@ __global__ void splitk_reduce_kernel(const float *__restrict__ ws, int splits, i
 
 constexpr int kGemmFillCtas = 2 * 152;  // about two waves of CTAs over the SMs
 
+// Products of at least this many multiply-adds run on the tensor cores.
+constexpr long long kTcMinMacs = 1ll << 24;
+
 template <bool TA, bool TB, int EPI>
 int gemm(const float *A, const float *B, float *C, int M, int N, int K, int lda, int ldb, int ldc,
          const float *bias, const float *mask, int ldm, cudaStream_t s) {
+  if ((long long)M * N * K >= kTcMinMacs) {
+    float *ws = nullptr;
+    int Mp = 0, Np = 0, rc = DISK_OK;
+    const int splits = tc::gemm_slices<TA, TB>(A, B, M, N, K, lda, ldb, &ws, &Mp, &Np, &rc, s);
+    if (!splits) return rc;
+    const long long MN = (long long)M * N;
+    const int blocks = (int)std::min<long long>((MN + 255) / 256, 152LL * 8);
+    splitk_reduce_kernel<EPI><<<blocks, 256, 0, s>>>(ws, splits, (long long)Mp * Np, Np, M, N, C,
+                                                     ldc, bias, mask, ldm);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(ws, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launch tensor-core reduce");
+    return DISK_OK;
+  }
   dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM);
   // a tile grid too small to fill the GPU splits K (slices of >= 128) and
   // sums the slices in a second pass
@@ -133,7 +157,8 @@ int gemm(const float *A, const float *B, float *C, int M, int N, int K, int lda,
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     const int blocks = (int)std::min<long long>((MN + 255) / 256, 152LL * 8);
-    splitk_reduce_kernel<EPI><<<blocks, 256, 0, s>>>(ws, splits, M, N, C, ldc, bias, mask, ldm);
+    splitk_reduce_kernel<EPI><<<blocks, 256, 0, s>>>(ws, splits, MN, N, M, N, C, ldc, bias, mask,
+                                                     ldm);
     e = cudaGetLastError();
   }
   cudaFreeAsync(ws, s);

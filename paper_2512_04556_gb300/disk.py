@@ -459,23 +459,18 @@ def fit(packed, sizes, L: int, T: int, steps: int, lr0: float = 1e-3, lr1: float
 def fit_autotune(packed, sizes, L: int, T: int, loss: int = LOSS_MSE, eps: float = 0.0,
                  stream=None) -> tuple:
     """Pick the fit kernel's launch configuration for this batch shape;
-    returns (threads per CTA, CTAs per cluster, kbig): targets of size >=
-    kbig are split over a whole cluster, smaller ones get one CTA each
-    (kbig = 0: every target split)."""
+    returns (threads per CTA, CTAs per target)."""
     out = ctypes.c_int()
     _check("disk_fit_autotune", lib().disk_fit_autotune(
         _vp(packed.data_ptr()), _int_arr(sizes), len(sizes), L, T, loss, eps,
         ctypes.byref(out), _stream(stream)))
-    v = out.value
-    return (v & 0xFFFF) // 16, v & 15, v >> 16
+    return out.value // 16, out.value % 16
 
 
-def fit_set_config(L: int, T: int, kmax: int, threads: int, ctas: int, kbig: int = 0):
-    """Record the fit launch configuration (threads per CTA, CTAs per cluster,
-    size from which a target is split over the cluster) for batches with this
-    L, T and largest target size."""
-    _check("disk_fit_set_config", lib().disk_fit_set_config(
-        L, T, kmax, (kbig << 16) | (threads * 16 + ctas)))
+def fit_set_config(L: int, T: int, kmax: int, threads: int, ctas: int):
+    """Record the fit launch configuration (threads per CTA, CTAs per target)
+    for batches with this L, T and largest target size."""
+    _check("disk_fit_set_config", lib().disk_fit_set_config(L, T, kmax, threads * 16 + ctas))
 
 
 def fit_loss_grad(packed, sizes, theta, loss: int = LOSS_MSE, eps: float = 0.0, stream=None):

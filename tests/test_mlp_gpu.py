@@ -45,6 +45,42 @@ def test_forward_and_train_step_match_oracle(torch_cuda):
     assert np.abs(upd[big] - wupd[big]).max() <= 1e-5
 
 
+def test_full_size_network_on_tensor_cores_matches_oracle(torch_cuda):
+    """The benchmark network (4096-512-512-512-192, batch 256): every product
+    runs on the tensor cores (four TF32 hi/lo products per FP32 product, split-K
+    over the SMs); forward, loss and gradient against the FP64 oracle at the
+    FP32 gate."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    shape = (4096, 512, 3, 192)
+    net = disk.MLP(*shape, seed=11)
+    p0 = net.params.cpu().numpy().astype(np.float64)
+    g = np.random.default_rng(12)
+    x = g.random((256, 4096)).astype(np.float32)
+    t = (0.5 * g.standard_normal((256, 192))).astype(np.float32)
+    dx, dt = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    y = net.forward(dx).cpu().numpy()
+    want, _ = mlp.forward(p0, x.astype(np.float64), *shape)
+    assert np.abs(y - want).max() <= 1e-5 * np.abs(want).max()
+    loss, grad = net.grad(dx, dt)
+    wl_, wg = mlp.loss_and_grad(p0, x.astype(np.float64), t.astype(np.float64), *shape)
+    assert abs(loss.item() - wl_) <= 1e-5 * wl_
+    gg = grad.cpu().numpy()
+    for (lo, hi) in _layer_ranges(shape):
+        ref = wg[lo:hi]
+        assert np.abs(gg[lo:hi] - ref).max() <= 1e-5 * np.abs(ref).max(), (lo, hi)
+
+
+def _layer_ranges(shape):
+    dims = mlp.layer_dims(*shape)
+    out, off = [], 0
+    for a, b in dims:
+        out.append((off, off + a * b))          # weights
+        out.append((off + a * b, off + a * b + b))  # biases
+        off += a * b + b
+    return out
+
+
 def test_area_resampling_matches_oracle(torch_cuda):
     torch = torch_cuda
     from paper_2512_04556_gb300 import disk
