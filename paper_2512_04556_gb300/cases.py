@@ -3,6 +3,8 @@ quick checks): ``python -m paper_2512_04556_gb300.cases <name> [--reps N]``.
 
   filter4k      4K RGB FP16, 8 x 8 fitted ellipse basis, L=4, T=24 (the benchmark frame,
                 autotuned tiles as the benchmark uses)
+  pair4k        the same frame with layers 1 and 2 fused into one launch (sv_pair_kernel),
+                layers 3 and 4 single (32 x 16, 32 x 32)
   backward4k    full backward (image and basis gradients) on the same frame
   dense4k       dense spatially varying convolution on the same frame
   gauss4k       4K RGB FP16 under a tilt-shift sigma map, 11 fitted Gaussians, L=6, T=8
@@ -43,7 +45,7 @@ def main(argv=None):
     p.add_argument("--reps", type=int, default=1)
     a = p.parse_args(argv)
     run = None
-    if a.name in ("filter4k", "backward4k", "dense4k"):
+    if a.name in ("filter4k", "pair4k", "backward4k", "dense4k"):
         img, maps = _frame4k()
         di, dm = torch.from_numpy(img).cuda(), torch.from_numpy(maps).cuda()
         if a.name == "dense4k":
@@ -54,6 +56,9 @@ def main(argv=None):
             b = disk.Basis.load(os.path.join(BASES, "ellipse8x8_L4T24.dkb"))
             if a.name == "filter4k":
                 disk.sv_filter_autotune(b, di, dm)      # the benchmark's tile choice
+                run = lambda: disk.sv_filter(b, di, dm)
+            elif a.name == "pair4k":
+                disk.sv_filter_set_layers(b, di, [8, 0, 2, 4])
                 run = lambda: disk.sv_filter(b, di, dm)
             else:
                 go = torch.empty_like(di).uniform_(-1, 1)
