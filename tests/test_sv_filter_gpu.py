@@ -277,7 +277,8 @@ def test_synth_flags_taps_beyond_declared_reach(torch_cuda):
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
 def test_tile_configurations_and_autotune(torch_cuda, dtype):
     """Both tile configurations match the oracle and each other bit for bit;
-    the autotuner picks one of them."""
+    the autotuner picks a tile per layer or a fused layer pair (code 8 then
+    0), with the same output."""
     torch = torch_cuda
     from paper_2512_04556_gb300 import disk
     n0, n1 = 3, 3
@@ -301,5 +302,10 @@ def test_tile_configurations_and_autotune(torch_cuda, dtype):
         want = want.astype(np.float16).astype(np.float64)
     assert rel_err(outs[2], want) <= (TOL32 if dtype == "f32" else TOL16)
     chosen = disk.sv_filter_autotune(b, t, m)
-    assert len(chosen) == 3 and set(chosen) <= {2, 4}
+    assert len(chosen) == 3 and set(chosen) <= {2, 4, 8, 0}
+    for l, c in enumerate(chosen):
+        if c == 8:
+            assert chosen[l + 1] == 0
+        if c == 0:
+            assert l > 0 and chosen[l - 1] == 8
     assert np.array_equal(disk.sv_filter(b, t, m).cpu().numpy(), outs[2])
