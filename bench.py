@@ -209,7 +209,8 @@ def run_disk(args, rank, world, dist):
     res = {"ms_per_step": ms, "value": value, "clocks": clk.summary(), "wall_s": wall,
            "tile": ("per layer (given): " if args.layers else "per layer (autotuned): ")
                    + ", ".join(tile_name(p) for p in tile_pix),
-           "gpu_launches": K * basis.L, "step_ms_min": float(np.min(step_ms)),
+           "gpu_launches": K * sum(1 for p in tile_pix if p != 0),
+           "step_ms_min": float(np.min(step_ms)),
            "step_ms_median": float(np.median(step_ms))}
     if rank == 0 and not args.no_extras:
         res.update(extras(basis, img, maps, d_img, d_maps, d_out, flush, ms, stream))
