@@ -12,6 +12,8 @@ quick checks): ``python -m paper_2512_04556_gb300.cases <name> [--reps N]``.
   bokeh4k       4K RGB FP16 rotational bokeh: 12 fitted aspect-2 ellipses (L=4, T=16) turned
   filter1080p   1080p RGB FP32, 16 fitted disks, L=4, T=16
   fit           64 uneven targets, L=4, T=16, 100 steps (sparse-sampling init)
+  fit256        the benchmark's 256 uneven targets, L=4, T=16, 100 steps, 512 threads x
+                4-CTA clusters per target (the benchmark's launch configuration)
   mlp           one training step of the learned initializer, batch 256
 """
 from __future__ import annotations
@@ -89,6 +91,11 @@ def main(argv=None):
     elif a.name == "fit":
         packed, sizes = disk.pack_targets(wl.shape_batch(64))
         run = lambda: disk.fit(packed, sizes, 4, 16, 100, init=disk.INIT_SS, seed=1)
+    elif a.name == "fit256":
+        tg = wl.shape_batch(256)
+        packed, sizes = disk.pack_targets(tg)
+        disk.fit_set_config(4, 16, max(sizes), 512, 4)
+        run = lambda: disk.fit(packed, sizes, 4, 16, 100, init=disk.INIT_SS, seed=7)
     elif a.name == "mlp":
         net = disk.MLP(4096, 512, 3, 192, seed=0)
         g = torch.Generator(device="cuda").manual_seed(0)
