@@ -618,14 +618,65 @@ def learned_init_leg():
     from paper_2512_04556_gb300 import learned_init as li
     c = wl.C5
     t0 = time.perf_counter()
-    res = li.run(n_train=c["train"], n_heldout=c["heldout"], epochs=30, steps=500,
-                 hidden=c["hidden"], depth=c["depth"])
+    res, net = li.run(n_train=c["train"], n_heldout=c["heldout"], epochs=30, steps=500,
+                      hidden=c["hidden"], depth=c["depth"], return_net=True)
     torch.cuda.synchronize()
     res["total_s"] = time.perf_counter() - t0
     res["target_speedup"] = 5.0
     res["config"] = (f"{c['train']} pairs, {c['heldout']} held-out, L={c['L']} T={c['T']}, "
                      f"input {c['side']}x{c['side']}")
+    res["fits_to_tau"] = learned_fits_leg(net)
     return res
+
+
+def learned_fits_leg(net, batch=256, steps_learned=100, steps_plain=500, reps=3):
+    """Fits per second to the fixed relative MSE on a fresh batch of 256
+    seeded targets (an index range disjoint from the network's training and
+    evaluation targets): the plain fitter (sparse-sampling start, 500 steps)
+    against the learned start (disk_learned_init) plus 100 steps; the
+    learned start's own cost is inside its timed region."""
+    import torch
+
+    from paper_2512_04556_gb300 import disk
+    from paper_2512_04556_gb300 import learned_init as li
+    tg = wl.shape_batch(batch, first=20_000_000)
+    packed, sizes = disk.pack_targets(tg)
+    energy = np.array([(t.astype(np.float64) ** 2).sum() for t in tg])
+    k2 = np.array([t.shape[0] ** 2 for t in tg], dtype=np.float64)
+    L, T = wl.C3["L"], wl.C3["T"]
+    disk.fit_autotune(packed, sizes, L, T)
+    out = {}
+
+    def timed(fn):
+        res = fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            res = fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts)), res
+
+    def plain():
+        return disk.fit(packed, sizes, L, T, steps_plain, init=disk.INIT_SS, seed=7)[1]
+
+    def learned():
+        th0, _ = disk.learned_init(net, packed, sizes, L, T, li.SIDE)
+        return disk.fit(packed, sizes, L, T, steps_learned, init=disk.INIT_GIVEN, theta=th0)[1]
+
+    for name, fn, steps in (("plain", plain, steps_plain), ("learned", learned, steps_learned)):
+        ms, final = timed(fn)
+        rel = final.cpu().numpy().astype(np.float64) * k2 / energy
+        reached = int((rel <= TAU_REL_MSE).sum())
+        out[name] = {"fits_per_s": reached / (ms * 1e-3), "ms_per_batch": ms, "steps": steps,
+                     "reached_tau": reached, "median_rel_mse": float(np.median(rel))}
+    out["batch"] = f"{batch} targets, shape_batch index range from 20,000,000 (held out)"
+    out["tau_rel_mse"] = TAU_REL_MSE
+    out["speedup"] = out["learned"]["fits_per_s"] / max(out["plain"]["fits_per_s"], 1e-9)
+    return out
 
 
 def fit_cpu_baseline(budget_s=10.0):

@@ -124,8 +124,9 @@ def evaluate(net, targets, L, T, steps=500):
 
 
 def run(n_train=50000, n_heldout=2000, epochs=30, steps=500, kmin=33, kmax=129, hidden=512,
-        depth=3, seed=0):
-    """Full learned-initializer experiment; returns a summary dict."""
+        depth=3, seed=0, return_net=False):
+    """Full learned-initializer experiment; returns a summary dict (and the
+    trained network with ``return_net``)."""
     import torch
     L, T = wl.C5["L"], wl.C5["T"]
     t0 = time.perf_counter()
@@ -147,7 +148,7 @@ def run(n_train=50000, n_heldout=2000, epochs=30, steps=500, kmin=33, kmax=129, 
     res.update({"train_pairs": n_train, "epochs": epochs, "pair_generation_s": t_pairs,
                 "training_s": t_train, "final_train_loss": log[-1] if log else None,
                 "network": f"{SIDE * SIDE}-{'-'.join([str(hidden)] * depth)}-{L * T * 3}"})
-    return res
+    return (res, net) if return_net else res
 
 
 if __name__ == "__main__":
