@@ -632,9 +632,10 @@ def learned_init_leg():
 def learned_fits_leg(net, batch=256, steps_learned=100, steps_plain=500, reps=3):
     """Fits per second to the fixed relative MSE on a fresh batch of 256
     seeded targets (an index range disjoint from the network's training and
-    evaluation targets): the plain fitter (sparse-sampling start, 500 steps)
-    against the learned start (disk_learned_init) plus 100 steps; the
-    learned start's own cost is inside its timed region."""
+    evaluation targets): the plain fitter (sparse-sampling start, 500 steps,
+    lr 1e-3 -> 1e-4) against the learned start (disk_learned_init) plus the
+    first 100 steps of that same schedule (5x fewer iterations); the learned
+    start's own cost is inside its timed region."""
     import torch
 
     from paper_2512_04556_gb300 import disk
@@ -663,9 +664,14 @@ def learned_fits_leg(net, batch=256, steps_learned=100, steps_plain=500, reps=3)
     def plain():
         return disk.fit(packed, sizes, L, T, steps_plain, init=disk.INIT_SS, seed=7)[1]
 
+    # the first steps_learned steps of the plain fitter's linear schedule
+    lr0, lr1 = 1e-3, 1e-4
+    lr1_cut = lr0 + (lr1 - lr0) * (steps_learned - 1) / (steps_plain - 1)
+
     def learned():
         th0, _ = disk.learned_init(net, packed, sizes, L, T, li.SIDE)
-        return disk.fit(packed, sizes, L, T, steps_learned, init=disk.INIT_GIVEN, theta=th0)[1]
+        return disk.fit(packed, sizes, L, T, steps_learned, lr0=lr0, lr1=lr1_cut,
+                        init=disk.INIT_GIVEN, theta=th0)[1]
 
     for name, fn, steps in (("plain", plain, steps_plain), ("learned", learned, steps_learned)):
         ms, final = timed(fn)
@@ -673,6 +679,7 @@ def learned_fits_leg(net, batch=256, steps_learned=100, steps_plain=500, reps=3)
         reached = int((rel <= TAU_REL_MSE).sum())
         out[name] = {"fits_per_s": reached / (ms * 1e-3), "ms_per_batch": ms, "steps": steps,
                      "reached_tau": reached, "median_rel_mse": float(np.median(rel))}
+    out["learned"]["lr"] = f"{lr0:g} -> {lr1_cut:.3g} (steps 0..{steps_learned - 1} of the 500-step schedule)"
     out["batch"] = f"{batch} targets, shape_batch index range from 20,000,000 (held out)"
     out["tau_rel_mse"] = TAU_REL_MSE
     out["speedup"] = out["learned"]["fits_per_s"] / max(out["plain"]["fits_per_s"], 1e-9)
