@@ -766,6 +766,17 @@ def oracle_full_frames():
     out["sv_4k_fp16_2d"] = {"s_per_frame_extrapolated": dt * H * W / (512 * 512),
                             "gpix_per_s": 512 * 512 / dt / 1e9,
                             "frame": "512x512 centre crop, extrapolated per pixel"}
+    # the dense spatially varying reference (81 x 81 ellipse node kernels on a
+    # 16 x 16 grid, Eq. 1 per pixel) on a 128 x 128 crop of the same frame
+    img_c, maps_c, _, _, _ = _oracle_crop(128, 128)
+    n0, n1 = np.linspace(2.0, 40.0, 16), np.linspace(0.0, 1.0, 16)
+    lut = wl.ellipse_lut(n0, n1, 81).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.dense_sv(img_c, maps_c, [16, 16], np.concatenate([n0, n1]), lut)
+    dt = time.perf_counter() - t0
+    out["dense_sv_4k_fp16_2d"] = {"s_per_frame_extrapolated": dt * H * W / (128 * 128),
+                                  "gpix_per_s": 128 * 128 / dt / 1e9,
+                                  "frame": "128x128 centre crop, 81x81 kernels, extrapolated"}
     return out
 
 
