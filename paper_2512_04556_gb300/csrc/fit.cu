@@ -423,8 +423,12 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
   __syncthreads();  // sh.g complete for the update
 }
 
+// 512-thread CTAs are held to 40 registers so that three fit on an SM: the
+// sweeps are bound by the latency of their canvas reads, and the extra warps
+// hide more of it than the few spilled values cost (225 against 233 ms for
+// the 256-target batch at 4 CTAs per target).
 template <int NT, int CL>
-__global__ void __launch_bounds__(NT) fit_kernel(FitArgs A) {
+__global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) fit_kernel(FitArgs A) {
   __shared__ FitShared sh;
   const unsigned rank = target_rank<CL>();
   const int b = A.order[blockIdx.x / CL];
