@@ -361,6 +361,36 @@ int disk_fit(const float *d_targets, const int *sizes, int batch, int L, int T,
              uint64_t seed, float *d_theta_io, float *d_final_loss,
              float *d_loss_hist, void *stream);
 
+/* Checkpointed form of disk_fit (same optimisation, Sec. 4.1 Eq. 4-5 with
+ * the Sec. 5.1 schedule): runs steps step0 .. step0+steps-1 of a fit whose
+ * learning rate decays linearly from lr0 to lr1 over total_steps steps, with
+ * the optimiser's state carried in d_state, so that a fit can be stopped,
+ * saved and continued.
+ * d_state: float [batch][3][L*T*3], per target the optimised variables (the
+ *   offsets in units of s_b, clamped to [-1, 1], and the raw weights, in the
+ *   [L][T][3] order of theta), then Adam's first and second moments in the
+ *   same order.  step0 == 0: the start is built as disk_fit builds it for
+ *   `init` and `seed` (DISK_INIT_GIVEN: from d_theta_io; moments zero) and
+ *   d_state's contents are ignored; step0 > 0: the state is read from d_state
+ *   (offsets clamped again, an identity on any state this call wrote), and
+ *   d_theta_io's contents, init and seed are ignored.  On return d_state holds
+ *   the state after the call's last step and d_theta_io the corresponding
+ *   complex (pixels).
+ * d_loss_hist: float [batch][steps+1], loss before each step of this call and
+ *   after its last (may be NULL).  d_final_loss as disk_fit.
+ * A fit of n steps split into calls [0, k) and [k, n) returns, bit for bit,
+ * what one disk_fit of n steps with the same init and seed returns, as long
+ * as both run in the same launch configuration (disk_fit_set_config).
+ * DISK_ERR_INVALID_ARG for a null d_state, a bad init, or unless
+ * 0 <= step0 <= step0 + steps <= total_steps <= 10^6.  Other arguments,
+ * limits, launches and scratch as disk_fit (the init kernel only when
+ * step0 == 0 and init is not DISK_INIT_GIVEN). */
+int disk_fit_resume(const float *d_targets, const int *sizes, int batch, int L, int T,
+                    int step0, int steps, int total_steps, float lr0, float lr1,
+                    int init, int loss, float eps, uint64_t seed, float *d_state,
+                    float *d_theta_io, float *d_final_loss, float *d_loss_hist,
+                    void *stream);
+
 /* Launch-configuration autotuner of disk_fit: times the persistent fit kernel
  * in each built configuration -- 256, 512 or 1024 threads per CTA, and one
  * CTA or a thread-block cluster of 2 or 4 CTAs (on as many SMs) per target --

@@ -61,7 +61,9 @@ struct FitArgs {
   float *loss_out;       // [batch] final loss (may be null)
   float *loss_hist;      // [batch][steps + 1] (may be null)
   float *grad_out;       // [batch][L][T][3] (loss-and-gradient mode only)
+  float *state;          // [batch][3][L*T*3]: q, Adam m, Adam v (may be null)
   int batch, L, T, steps, loss_kind, mode;  // mode 0 = fit, 1 = loss and gradient
+  int step0, total;      // this call runs steps step0 .. step0+steps-1 of total
   float eps, lr0, lr1;
 };
 
@@ -442,16 +444,25 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) fit_kernel(FitArgs A) {
   const float *tgt = A.targets + m.tgt_off;
   float *th = A.theta + (size_t)b * P;
   const float s = m.s;
+  float *st = A.state ? A.state + (size_t)b * 3 * P : nullptr;
+  const bool resume = st && A.step0 > 0;
   for (int j = threadIdx.x; j < P; j += blockDim.x) {
-    const float v = th[j];
-    sh.q[j] = (j % 3 == 2) ? v : fminf(fmaxf(v / s, -1.f), 1.f);
-    sh.mo[j] = 0.f;
-    sh.vo[j] = 0.f;
+    // a resumed state is clamped again: an identity on any state this kernel
+    // wrote, and it keeps the taps of a corrupted one inside the canvases
+    const float v = resume ? st[j] : th[j];
+    sh.q[j] = (j % 3 == 2) ? v : fminf(fmaxf(resume ? v : v / s, -1.f), 1.f);
+    sh.mo[j] = resume ? st[P + j] : 0.f;
+    sh.vo[j] = resume ? st[2 * P + j] : 0.f;
   }
   __syncthreads();
   const float b1 = 0.9f, b2 = 0.999f, aeps = 1e-8f;
   float b1t = 1.f, b2t = 1.f;
-  for (int step = 0; step < A.steps || (A.mode == 1 && step == 0); ++step) {
+  for (int k = 0; k < A.step0; ++k) {  // the same products an unbroken run forms
+    b1t *= b1;
+    b2t *= b2;
+  }
+  for (int it = 0; it < A.steps || (A.mode == 1 && it == 0); ++it) {
+    const int step = A.step0 + it;
     make_taps(sh, L, T, s);
     const float loss = forward_loss<CL>(sh, A, m, act, ga, tgt, rank);
     backward<CL>(sh, A, m, act, ga, gb, rank);
@@ -464,8 +475,8 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) fit_kernel(FitArgs A) {
       return;
     }
     if (rank == 0 && threadIdx.x == 0 && A.loss_hist)
-      A.loss_hist[(size_t)b * (A.steps + 1) + step] = loss;
-    const float lr = A.steps > 1 ? A.lr0 + (A.lr1 - A.lr0) * (float)step / (float)(A.steps - 1) : A.lr0;
+      A.loss_hist[(size_t)b * (A.steps + 1) + it] = loss;
+    const float lr = A.total > 1 ? A.lr0 + (A.lr1 - A.lr0) * (float)step / (float)(A.total - 1) : A.lr0;
     b1t *= b1;
     b2t *= b2;
     for (int j = threadIdx.x; j < P; j += blockDim.x) {
@@ -489,8 +500,14 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) fit_kernel(FitArgs A) {
       if (A.loss_out) A.loss_out[b] = loss;
       if (A.loss_hist) A.loss_hist[(size_t)b * (A.steps + 1) + A.steps] = loss;
     }
-    for (int j = threadIdx.x; j < P; j += blockDim.x)
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
       th[j] = (j % 3 == 2) ? sh.q[j] : sh.q[j] * s;
+      if (st) {
+        st[j] = sh.q[j];
+        st[P + j] = sh.mo[j];
+        st[2 * P + j] = sh.vo[j];
+      }
+    }
   }
   target_sync<CL>();  // no CTA leaves while another may read its shared memory
 }
@@ -607,7 +624,8 @@ constexpr int kFitConfigs[] = {256 * 16 + 1, 512 * 16 + 1, 1024 * 16 + 1, 512 * 
 int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, int steps,
             float lr0, float lr1, int init, int loss, float eps, unsigned long long seed,
             float *d_theta, float *d_loss, float *d_hist, float *d_grad, int mode,
-            cudaStream_t s, int config = 0) {
+            cudaStream_t s, int config = 0, float *d_state = nullptr, int step0 = 0,
+            int total = -1) {
   if (!d_targets || !sizes || !d_theta) return fail(DISK_ERR_INVALID_ARG, "null pointer");
   if (batch < 1 || L < 1 || L > DISK_MAX_LAYERS || T < 1 || T > DISK_MAX_TAPS)
     return fail(DISK_ERR_INVALID_ARG, "batch >= 1, L in [1, 16], T in [1, 64] required");
@@ -655,6 +673,9 @@ int run_fit(const float *d_targets, const int *sizes, int batch, int L, int T, i
   A.loss_out = d_loss;
   A.loss_hist = d_hist;
   A.grad_out = d_grad;
+  A.state = d_state;
+  A.step0 = step0;
+  A.total = total < 0 ? steps : total;
   A.batch = batch; A.L = L; A.T = T; A.steps = steps; A.loss_kind = loss; A.mode = mode;
   A.eps = eps; A.lr0 = lr0; A.lr1 = lr1;
   if (mode == 0 && init != 0) fit_init_kernel<<<batch, kFitThreads, 0, s>>>(A, init, seed);
@@ -679,6 +700,21 @@ extern "C" int disk_fit(const float *d_targets, const int *sizes, int batch, int
   return run_fit(d_targets, sizes, batch, L, T, steps, lr0, lr1, init, loss, eps, seed,
                  d_theta_io, d_final_loss, d_loss_hist, nullptr, 0,
                  static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int disk_fit_resume(const float *d_targets, const int *sizes, int batch, int L,
+                               int T, int step0, int steps, int total_steps, float lr0,
+                               float lr1, int init, int loss, float eps, uint64_t seed,
+                               float *d_state, float *d_theta_io, float *d_final_loss,
+                               float *d_loss_hist, void *stream) {
+  if (!d_state) return fail(DISK_ERR_INVALID_ARG, "null optimiser state");
+  if (step0 < 0 || steps < 0 || total_steps > 1000000 || steps > total_steps - step0)
+    return fail(DISK_ERR_INVALID_ARG, "need 0 <= step0 <= step0 + steps <= total_steps <= 1e6");
+  if (init < 0 || init > 3) return fail(DISK_ERR_INVALID_ARG, "bad init");
+  return run_fit(d_targets, sizes, batch, L, T, steps, lr0, lr1,
+                 step0 > 0 ? (int)DISK_INIT_GIVEN : init, loss, eps, seed,
+                 d_theta_io, d_final_loss, d_loss_hist, nullptr, 0,
+                 static_cast<cudaStream_t>(stream), 0, d_state, step0, total_steps);
 }
 
 extern "C" int disk_fit_loss_grad(const float *d_targets, const int *sizes, int batch, int L,

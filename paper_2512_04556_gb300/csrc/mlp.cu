@@ -175,9 +175,12 @@ __global__ void colsum_kernel(const float *D, float *db, int M, int N) {
   db[n] = s;
 }
 
-// MSE over the batch and outputs: loss (accumulated into *loss, pre-zeroed)
-// and dY = 2 (y - t) / (M N).
-__global__ void mse_kernel(const float *y, const float *t, float *dy, long long n, float *loss) {
+// MSE over the batch and outputs: loss (stored to *loss) and
+// dY = 2 (y - t) / (M N).  One block (launched with kMseThreads threads), so
+// the sum is taken in a fixed order and the loss is reproducible bit for bit.
+constexpr int kMseThreads = 1024;
+__global__ void __launch_bounds__(kMseThreads) mse_kernel(const float *y, const float *t,
+                                                          float *dy, long long n, float *loss) {
   __shared__ float red[32];
   float part = 0.f;
   const float inv = 1.f / (float)n;
@@ -193,7 +196,7 @@ __global__ void mse_kernel(const float *y, const float *t, float *dy, long long 
   if (threadIdx.x == 0) {
     float s = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-    atomicAdd(loss, s);
+    *loss = s;
   }
 }
 
@@ -368,11 +371,8 @@ int mlp_grad(const Shape &sh, const float *d_params, const float *d_x, const flo
   int rc = mlp_forward(sh, d_params, d_x, batch, y, acts, nullptr, s);
   cudaError_t e = cudaSuccess;
   if (rc == DISK_OK) {
-    e = cudaMemsetAsync(d_loss, 0, sizeof(float), s);
-    if (e == cudaSuccess) {
-      mse_kernel<<<64, 256, 0, s>>>(y, d_target, d0, ny, d_loss);
-      e = cudaGetLastError();
-    }
+    mse_kernel<<<1, kMseThreads, 0, s>>>(y, d_target, d0, ny, d_loss);
+    e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "mse");
   }
   // backward: d holds dL/d(output of layer i)

@@ -78,6 +78,9 @@ def lib() -> ctypes.CDLL:
             "disk_synth_kernel": (_i, [_vp, _i, _i, _i, _i, ctypes.c_float, _vp, _vp]),
             "disk_fit": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, ctypes.c_float, _i, _i,
                               ctypes.c_float, ctypes.c_uint64, _vp, _vp, _vp, _vp]),
+            "disk_fit_resume": (_i, [_vp, _ip, _i, _i, _i, _i, _i, _i, ctypes.c_float,
+                                     ctypes.c_float, _i, _i, ctypes.c_float, ctypes.c_uint64,
+                                     _vp, _vp, _vp, _vp, _vp]),
             "disk_fit_autotune": (_i, [_vp, _ip, _i, _i, _i, _i, ctypes.c_float, _ip, _vp]),
             "disk_sv_filter_set_layers": (_i, [_vp, _i, _i, _i, _i, _ip]),
             "disk_fit_set_config": (_i, [_i, _i, _i, _i]),
@@ -456,6 +459,32 @@ def fit(packed, sizes, L: int, T: int, steps: int, lr0: float = 1e-3, lr1: float
     return theta, final, hist
 
 
+def fit_resume(packed, sizes, state, theta, step0: int, steps: int, total_steps: int,
+               lr0: float = 1e-3, lr1: float = 1e-4, init: int = INIT_GIVEN,
+               loss: int = LOSS_MSE, eps: float = 0.0, seed: int = 0, loss_hist: bool = False,
+               stream=None):
+    """Steps step0 .. step0+steps-1 of a total_steps-step fit (Eq. 4), the
+    optimiser's state carried in `state` [batch, 3, L*T*3] (updated in place;
+    built from `init`/`seed`/`theta` when step0 == 0) and the complex in
+    `theta` [batch, L, T, 3] (pixels, updated in place).  Returns (final loss
+    [batch], history [batch, steps+1] or None)."""
+    import torch
+    batch, L, T, _ = theta.shape
+    if tuple(state.shape) != (batch, 3, L * T * 3) or state.dtype != torch.float32 \
+            or not state.is_contiguous():
+        raise ValueError(f"state must be contiguous float32 [{batch}, 3, {L * T * 3}]")
+    if theta.dtype != torch.float32 or not theta.is_contiguous():
+        raise ValueError("theta must be a contiguous float32 tensor [batch, L, T, 3]")
+    dev = packed.device
+    final = torch.empty(batch, device=dev, dtype=torch.float32)
+    hist = torch.empty((batch, steps + 1), device=dev, dtype=torch.float32) if loss_hist else None
+    _check("disk_fit_resume", lib().disk_fit_resume(
+        _vp(packed.data_ptr()), _int_arr(sizes), batch, L, T, step0, steps, total_steps, lr0, lr1,
+        init, loss, eps, seed, _vp(state.data_ptr()), _vp(theta.data_ptr()), _vp(final.data_ptr()),
+        _vp(hist.data_ptr()) if hist is not None else None, _stream(stream)))
+    return final, hist
+
+
 def fit_autotune(packed, sizes, L: int, T: int, loss: int = LOSS_MSE, eps: float = 0.0,
                  stream=None) -> tuple:
     """Pick the fit kernel's launch configuration for this batch shape;
@@ -528,6 +557,29 @@ class MLP:
         _check("disk_mlp_adam", lib().disk_mlp_adam(
             _vp(self.params.data_ptr()), _vp(self.m.data_ptr()), _vp(self.v.data_ptr()),
             _vp(grad.data_ptr()), self.step, lr, *self.shape, _stream(stream)))
+
+    def save(self, path: str):
+        """Writes the parameters, both Adam moments and the step count to a
+        checkpoint file; `MLP.load` continues training from it exactly."""
+        from . import checkpoint
+        checkpoint.save_mlp(path, shape=self.shape, step=self.step, params=self.params,
+                            m=self.m, v=self.v)
+
+    @classmethod
+    def load(cls, path: str, device="cuda") -> "MLP":
+        """The network (and optimiser state) of a checkpoint file."""
+        import torch
+
+        from . import checkpoint
+        shape, step, p, m, v = checkpoint.load_mlp(path)
+        net = cls(*shape, device=device)
+        if p.size != net.params.numel():
+            raise checkpoint.CheckpointError(
+                f"{path}: {p.size} parameters, shape {shape} has {net.params.numel()}")
+        for name, a in (("params", p), ("m", m), ("v", v)):
+            getattr(net, name).copy_(torch.from_numpy(a))
+        net.step = step
+        return net
 
     def train_step(self, x, target, lr: float, stream=None):
         """One Adam step on the batch; returns the loss as a device tensor."""

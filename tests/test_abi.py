@@ -53,6 +53,15 @@ def test_validation_rejects_before_any_device_work(lib):
     assert disk.lib().disk_basis_load(b"/nonexistent/basis.dkb", ctypes.byref(h)) == -2
     rc = disk.lib().disk_sv_filter(None, None, 0, None, 0, 8, 8, 3, 0, None, None)
     assert rc == -1
+    sizes = (ctypes.c_int * 1)(9)
+    rc = disk.lib().disk_fit_resume(None, sizes, 1, 2, 4, 0, 5, 5, 1e-3, 1e-4, 0, 0, 0.0, 0,
+                                    None, None, None, None, None)
+    assert rc == -1 and b"state" in disk.lib().disk_last_error_message()
+    fake = ctypes.c_void_p(256)  # never dereferenced: the schedule check fails first
+    for step0, steps, total in ((3, 3, 5), (-1, 2, 5), (0, -1, 5), (0, 2, 2000000)):
+        rc = disk.lib().disk_fit_resume(fake, sizes, 1, 2, 4, step0, steps, total, 1e-3, 1e-4,
+                                        0, 0, 0.0, 0, fake, fake, None, None, None)
+        assert rc == -1 and b"step0" in disk.lib().disk_last_error_message()
 
 
 def test_basis_file_rejects_corruption(tmp_path, lib):
