@@ -11,12 +11,15 @@
 // fixed order, so every CTA applies the same Adam update.  Per step:
 //   forward   impulse on a zero-padded canvas, L shift-invariant layers, each
 //             computed only on its support box S_l = H_1 + ... + H_l, with
-//             H_l = ceil(max |o_l|) + 1 from the current taps;
+//             H_l = ceil(max |o_l|) + 1 from the current taps; the first
+//             layer in closed form (its output is T bilinear splats);
 //   loss      MSE (or Charbonnier, Eq. 11) over the plane, target zero-padded;
 //   backward  dL/dI_L, then per layer the tap gradients (one warp per tap,
 //             warp-shuffle reductions) and the adjoint plane, which on a
 //             zero-bounded canvas is the same layer applied at -o (the
-//             bilinear tent is symmetric) -- a gather, no atomics;
+//             bilinear tent is symmetric) -- a gather, no atomics; the first
+//             layer's tap gradients in closed form from the four pixels per
+//             tap where its sums are non-zero;
 //   update    Adam with linearly decayed lr on offsets in units of the target
 //             half-width s (clamped to |o/s| <= 1) and raw weights.
 // All L+1 activations stay in a per-target scratch region (L2-resident for
@@ -245,6 +248,10 @@ struct FitShared {
   PreparedTaps pt;  // the layer being swept
   float red[kFitMaxWarps];
   float closs;  // this CTA's share of the loss
+  // the first layer's non-zero output pixels (closed form, rank 0 only)
+  int splat_pix[4 * DISK_MAX_TAPS];
+  float splat_val[4 * DISK_MAX_TAPS];
+  int nsplat;
   // per-(chunk, tap) partial tap gradients of the warps of this CTA, two
   // buffers used by alternate layers
   static constexpr int kPart = 3 * (kFitMaxWarps * kFitMaxCluster > DISK_MAX_TAPS
@@ -301,6 +308,94 @@ __device__ void make_taps(FitShared &sh, int L, int T, float s) {
   __syncthreads();
 }
 
+// The first layer of the cascade in closed form.  Its input is the unit
+// impulse at the centre c, so the gather dst[p] = sum_i w_i bilinear(I_0,
+// p + o_i) is non-zero only at the four pixels p = c - n_i - e of every tap
+// (n_i the clamped floor of o_i, e in {0, 1}^2 the corner of the bilinear
+// footprint that lands on c), where it receives the tap's corner weight; a
+// pixel that several taps reach gets their sum in tap order, as the gather
+// forms it.  The plane act[1] is therefore kept zero except at these <= 4T
+// pixels: it is zeroed once when the fit starts, and every step clears the
+// previous step's pixels before it writes the new ones.  Run by one CTA (the
+// cluster's rank 0); the caller's barrier publishes the plane.
+__device__ void splat_first_layer(FitShared &sh, float *dst, int R, int T) {
+  const int N = 2 * R + 1, n = 4 * T;
+  prepare_taps(sh.pt, sh.taps, T, sh.ext[0].H, 1.f, R);
+  for (int k = threadIdx.x; k < sh.nsplat; k += blockDim.x) dst[sh.splat_pix[k]] = 0.f;
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int i = k >> 2, ex = k & 1, ey = (k >> 1) & 1;
+    const float4 w = sh.pt.w[i];
+    sh.splat_pix[k] = R * N + R - sh.pt.off[i] - ey * N - ex;
+    sh.splat_val[k] = ey ? (ex ? w.w : w.z) : (ex ? w.y : w.x);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int p = sh.splat_pix[k];
+    bool first = true;
+    for (int j = 0; j < k && first; ++j) first = sh.splat_pix[j] != p;
+    if (first) {
+      float acc = 0.f;
+      for (int j = k; j < n; ++j)
+        if (sh.splat_pix[j] == p) acc += sh.splat_val[j];
+      dst[p] = acc;
+    }
+  }
+  if (threadIdx.x == 0) sh.nsplat = n;
+}
+
+// Tap gradients of the first layer in closed form.  With the impulse as the
+// layer's input, the terms of the tap-gradient sums over the layer's box
+// vanish except at the four pixels p = c - n_i - e of the tap, where the
+// bilinear corner values are 1 at e and 0 at the other three corners.  The
+// sums' factor dL/dI_1 at those pixels is G itself when L = 1, else the
+// adjoint of the second layer applied to G = dL/dI_2 (sh.pt holding that
+// layer's taps prepared at -o), evaluated only there.  Every CTA of a cluster
+// computes all of them (the same arithmetic on the same data) into sh.g.
+__device__ void first_layer_grads(FitShared &sh, const float *G, int R, int T, bool adjoint) {
+  const int N = 2 * R + 1, n = 4 * T, halo = sh.ext[0].H;
+  const int lanes = (n + 31) & ~31;  // whole warps: the shuffles below
+  for (int k = threadIdx.x; k < lanes; k += blockDim.x) {
+    const bool valid = k < n;
+    const int i = valid ? k >> 2 : 0, ex = k & 1, ey = (k >> 1) & 1;
+    const float4 t = sh.taps[i];
+    float fx, fy;
+    const int nx = min(max(split_floor(t.x, fx), -halo), halo - 1);
+    const int ny = min(max(split_floor(t.y, fy), -halo), halo - 1);
+    const int p = (R - ny - ey) * N + (R - nx - ex);
+    float g = 0.f;
+    if (valid) {
+      if (adjoint) {
+        for (int j = 0; j < T; ++j) {
+          const float4 w = sh.pt.w[j];
+          const float *q = G + p + sh.pt.off[j];
+          g += w.x * q[0] + w.y * q[1] + w.z * q[N] + w.w * q[N + 1];
+        }
+      } else {
+        g = G[p];
+      }
+    }
+    // the sweep's expressions with the corner values (a, b; c, d)
+    const float a = (ex == 0 && ey == 0) ? 1.f : 0.f, b = (ex == 1 && ey == 0) ? 1.f : 0.f;
+    const float c = (ex == 0 && ey == 1) ? 1.f : 0.f, d = (ex == 1 && ey == 1) ? 1.f : 0.f;
+    const float top = a + fx * (b - a), bot = c + fx * (d - c);
+    float gw = g * (top + fy * (bot - top));
+    float gdx = g * ((1.f - fy) * (b - a) + fy * (d - c));
+    float gdy = g * (bot - top);
+    // the tap's four pixels are lanes 4i .. 4i+3: summed in a fixed order
+    for (int o = 1; o <= 2; o <<= 1) {
+      gw += __shfl_xor_sync(0xffffffffu, gw, o);
+      gdx += __shfl_xor_sync(0xffffffffu, gdx, o);
+      gdy += __shfl_xor_sync(0xffffffffu, gdy, o);
+    }
+    if (valid && (k & 3) == 0) {
+      sh.g[i * 3] = gdx * t.z;
+      sh.g[i * 3 + 1] = gdy * t.z;
+      sh.g[i * 3 + 2] = gw;
+    }
+  }
+}
+
 // Forward cascade on planes act[0..L]; returns the loss and leaves dL/dI_L in
 // gL (box of half-width max(S_L, h)).  Sweeps are split over the CL CTAs.
 template <int CL>
@@ -308,16 +403,9 @@ __device__ float forward_loss(FitShared &sh, const FitArgs &A, const FitMeta &m,
                               float *gL, const float *tgt, unsigned rank) {
   const int L = A.L, T = A.T, R = m.R, N = 2 * R + 1, K = m.K, h = (K - 1) / 2;
   const int tid = (int)rank * blockDim.x + threadIdx.x, nthr = blockDim.x * CL;
-  {
-    // the footprint layer 1 reads: zeros, with the unit impulse at c
-    const int b0 = min(2 * sh.ext[0].H, R), side0 = 2 * b0 + 1;
-    for (int j = tid; j < side0 * side0; j += nthr) {
-      const int v = j / side0 - b0, u = j % side0 - b0;
-      act[0][(R + v) * N + (R + u)] = (u == 0 && v == 0) ? 1.f : 0.f;
-    }
-  }
+  if (rank == 0) splat_first_layer(sh, act[1], R, T);
   target_sync<CL>();
-  for (int l = 0; l < L; ++l) {
+  for (int l = 1; l < L; ++l) {
     const int S = sh.ext[l].S;
     prepare_taps(sh.pt, sh.taps + l * T, T, sh.ext[l].H, 1.f, R);
     __syncthreads();
@@ -364,7 +452,7 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
   const int nwt = nw * CL, gwarp = (int)rank * nw + warp;
   const int tid = (int)rank * blockDim.x + threadIdx.x, nthr = blockDim.x * CL;
   float *G = ga, *Gn = gb;
-  for (int l = L - 1; l >= 0; --l) {
+  for (int l = L - 1; l >= 1; --l) {  // the first layer: closed form, below
     const int S = sh.ext[l].S, halo = sh.ext[l].H;
     const float *prev = act[l];
     // this layer's partial-sum buffer: the other one may still be read by
@@ -402,12 +490,15 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
         pp[0] = gdx * t.z; pp[1] = gdy * t.z; pp[2] = gw;
       }
     }
-    if (l > 0) {
-      // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
-      // (reads G like the tap gradients above, writes the other plane)
-      prepare_taps(sh.pt, sh.taps + l * T, T, halo, -1.f, R);
-      __syncthreads();
+    // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
+    // (reads G like the tap gradients above, writes the other plane); for
+    // l = 1 only at the pixels the first layer's closed-form gradients read
+    prepare_taps(sh.pt, sh.taps + l * T, T, halo, -1.f, R);
+    __syncthreads();
+    if (l > 1) {
       canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.pt, T, tid, nthr);
+    } else {
+      first_layer_grads(sh, G, R, T, true);
     }
     // the partial sums and the adjoint plane are complete everywhere
     target_sync<CL>();
@@ -422,6 +513,7 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     }
     float *t = G; G = Gn; Gn = t;
   }
+  if (L == 1) first_layer_grads(sh, ga, R, T, false);
   __syncthreads();  // sh.g complete for the update
 }
 
@@ -454,7 +546,12 @@ __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) fit_kernel(FitArgs A) {
     sh.mo[j] = resume ? st[P + j] : 0.f;
     sh.vo[j] = resume ? st[2 * P + j] : 0.f;
   }
-  __syncthreads();
+  // the first layer's output plane is kept zero away from its splat pixels
+  for (long long j = (long long)rank * blockDim.x + threadIdx.x; j < (long long)plane;
+       j += (long long)blockDim.x * CL)
+    act[1][j] = 0.f;
+  if (threadIdx.x == 0) sh.nsplat = 0;
+  target_sync<CL>();
   const float b1 = 0.9f, b2 = 0.999f, aeps = 1e-8f;
   float b1t = 1.f, b2t = 1.f;
   for (int k = 0; k < A.step0; ++k) {  // the same products an unbroken run forms
