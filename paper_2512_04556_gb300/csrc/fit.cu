@@ -17,9 +17,10 @@
 //   backward  dL/dI_L, then per layer the tap gradients (one warp per tap,
 //             warp-shuffle reductions) and the adjoint plane, which on a
 //             zero-bounded canvas is the same layer applied at -o (the
-//             bilinear tent is symmetric) -- a gather, no atomics; the first
-//             layer's tap gradients in closed form from the four pixels per
-//             tap where its sums are non-zero;
+//             bilinear tent is symmetric) -- a gather, no atomics; the
+//             first layer's tap gradients in closed form from the four pixels
+//             per tap where its sums are non-zero, the second layer's as sums
+//             over the first layer's <= 4T non-zero output pixels;
 //   update    Adam with linearly decayed lr on offsets in units of the target
 //             half-width s (clamped to |o/s| <= 1) and raw weights.
 // All L+1 activations stay in a per-target scratch region (L2-resident for
@@ -316,32 +317,40 @@ __device__ void make_taps(FitShared &sh, int L, int T, float s) {
 // pixel that several taps reach gets their sum in tap order, as the gather
 // forms it.  The plane act[1] is therefore kept zero except at these <= 4T
 // pixels: it is zeroed once when the fit starts, and every step clears the
-// previous step's pixels before it writes the new ones.  Run by one CTA (the
-// cluster's rank 0); the caller's barrier publishes the plane.
-__device__ void splat_first_layer(FitShared &sh, float *dst, int R, int T) {
-  const int N = 2 * R + 1, n = 4 * T;
+// previous step's pixels before it writes the new ones.  Every CTA builds the
+// list (entry k = 4i + e: pixel splat_pix[k], and in splat_val[k] the pixel's
+// value at its first entry, 0 at repeated ones); only the CTA with `write`
+// (the cluster's rank 0) writes the plane, which the caller's barrier
+// publishes.  One entry per thread: every fit CTA has at least
+// 4 * DISK_MAX_TAPS threads.
+__device__ void splat_first_layer(FitShared &sh, float *dst, int R, int T, bool write) {
+  const int N = 2 * R + 1, n = 4 * T, k = threadIdx.x;
   prepare_taps(sh.pt, sh.taps, T, sh.ext[0].H, 1.f, R);
-  for (int k = threadIdx.x; k < sh.nsplat; k += blockDim.x) dst[sh.splat_pix[k]] = 0.f;
+  if (write)
+    for (int j = threadIdx.x; j < sh.nsplat; j += blockDim.x) dst[sh.splat_pix[j]] = 0.f;
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  if (k < n) {
     const int i = k >> 2, ex = k & 1, ey = (k >> 1) & 1;
     const float4 w = sh.pt.w[i];
     sh.splat_pix[k] = R * N + R - sh.pt.off[i] - ey * N - ex;
     sh.splat_val[k] = ey ? (ex ? w.w : w.z) : (ex ? w.y : w.x);
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  float acc = 0.f;
+  bool first = false;
+  if (k < n) {
     const int p = sh.splat_pix[k];
-    bool first = true;
+    first = true;
     for (int j = 0; j < k && first; ++j) first = sh.splat_pix[j] != p;
     if (first) {
-      float acc = 0.f;
       for (int j = k; j < n; ++j)
         if (sh.splat_pix[j] == p) acc += sh.splat_val[j];
-      dst[p] = acc;
+      if (write) dst[p] = acc;
     }
   }
-  if (threadIdx.x == 0) sh.nsplat = n;
+  __syncthreads();
+  if (k < n) sh.splat_val[k] = first ? acc : 0.f;
+  if (k == 0) sh.nsplat = n;
 }
 
 // Tap gradients of the first layer in closed form.  With the impulse as the
@@ -396,6 +405,41 @@ __device__ void first_layer_grads(FitShared &sh, const float *G, int R, int T, b
   }
 }
 
+// Tap gradients of the second layer from its sparse input.  I_1 is zero
+// except at the first layer's splat pixels y (values v_y, sh.splat_val), and
+// every term of the tap-gradient sums is linear in the four bilinear corners
+// (a, b; c, d) it reads, so the sums over the layer's box regroup as sums
+// over y of v_y times G at the four pixels that read y as a, b, c or d
+// (y - n_j, y - n_j - 1, y - n_j - N, y - n_j - N - 1).  G = dL/dI_2.
+// One warp per tap; every CTA of a cluster computes all of them into sh.g.
+__device__ void second_layer_grads(FitShared &sh, const float *G, int R, int T) {
+  const int N = 2 * R + 1, n = 4 * T, halo = sh.ext[1].H;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < T; j += nw) {
+    const float4 t = sh.taps[T + j];
+    float fx, fy;
+    const int nx = min(max(split_floor(t.x, fx), -halo), halo - 1);
+    const int ny = min(max(split_floor(t.y, fy), -halo), halo - 1);
+    const int off = ny * N + nx;
+    const float gx = 1.f - fx, gy = 1.f - fy;
+    float gw = 0.f, gdx = 0.f, gdy = 0.f;
+    for (int k = lane; k < n; k += 32) {
+      const float v = sh.splat_val[k];
+      const float *q = G + (sh.splat_pix[k] - off);
+      const float ga = q[0], gb = q[-1], gc = q[-N], gd = q[-N - 1];
+      gw += v * (gy * (gx * ga + fx * gb) + fy * (gx * gc + fx * gd));
+      gdx += v * (gy * (gb - ga) + fy * (gd - gc));
+      gdy += v * (gx * (gc - ga) + fx * (gd - gb));
+    }
+    gw = warp_sum(gw); gdx = warp_sum(gdx); gdy = warp_sum(gdy);
+    if (lane == 0) {
+      sh.g[(T + j) * 3] = gdx * t.z;
+      sh.g[(T + j) * 3 + 1] = gdy * t.z;
+      sh.g[(T + j) * 3 + 2] = gw;
+    }
+  }
+}
+
 // Forward cascade on planes act[0..L]; returns the loss and leaves dL/dI_L in
 // gL (box of half-width max(S_L, h)).  Sweeps are split over the CL CTAs.
 template <int CL>
@@ -403,7 +447,7 @@ __device__ float forward_loss(FitShared &sh, const FitArgs &A, const FitMeta &m,
                               float *gL, const float *tgt, unsigned rank) {
   const int L = A.L, T = A.T, R = m.R, N = 2 * R + 1, K = m.K, h = (K - 1) / 2;
   const int tid = (int)rank * blockDim.x + threadIdx.x, nthr = blockDim.x * CL;
-  if (rank == 0) splat_first_layer(sh, act[1], R, T);
+  splat_first_layer(sh, act[1], R, T, rank == 0);
   target_sync<CL>();
   for (int l = 1; l < L; ++l) {
     const int S = sh.ext[l].S;
@@ -452,7 +496,7 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
   const int nwt = nw * CL, gwarp = (int)rank * nw + warp;
   const int tid = (int)rank * blockDim.x + threadIdx.x, nthr = blockDim.x * CL;
   float *G = ga, *Gn = gb;
-  for (int l = L - 1; l >= 1; --l) {  // the first layer: closed form, below
+  for (int l = L - 1; l >= 2; --l) {  // the first two layers: closed forms, below
     const int S = sh.ext[l].S, halo = sh.ext[l].H;
     const float *prev = act[l];
     // this layer's partial-sum buffer: the other one may still be read by
@@ -491,15 +535,10 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
       }
     }
     // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
-    // (reads G like the tap gradients above, writes the other plane); for
-    // l = 1 only at the pixels the first layer's closed-form gradients read
+    // (reads G like the tap gradients above, writes the other plane)
     prepare_taps(sh.pt, sh.taps + l * T, T, halo, -1.f, R);
     __syncthreads();
-    if (l > 1) {
-      canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.pt, T, tid, nthr);
-    } else {
-      first_layer_grads(sh, G, R, T, true);
-    }
+    canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.pt, T, tid, nthr);
     // the partial sums and the adjoint plane are complete everywhere
     target_sync<CL>();
     for (int j = threadIdx.x; j < T * 3; j += blockDim.x) {
@@ -513,7 +552,17 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     }
     float *t = G; G = Gn; Gn = t;
   }
-  if (L == 1) first_layer_grads(sh, ga, R, T, false);
+  // G = dL/dI_min(L, 2), complete in every CTA's view: the first two layers'
+  // gradients read it at a few pixels each, redundantly in every CTA, so they
+  // need no exchange and no cluster barrier
+  if (L >= 2) {
+    prepare_taps(sh.pt, sh.taps + T, T, sh.ext[1].H, -1.f, R);
+    __syncthreads();
+    second_layer_grads(sh, G, R, T);
+    first_layer_grads(sh, G, R, T, true);
+  } else {
+    first_layer_grads(sh, G, R, T, false);
+  }
   __syncthreads();  // sh.g complete for the update
 }
 
@@ -523,6 +572,7 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
 // the 256-target batch at 4 CTAs per target).
 template <int NT, int CL>
 __global__ void __launch_bounds__(NT, NT == 512 ? 3 : 1) fit_kernel(FitArgs A) {
+  static_assert(NT >= 4 * DISK_MAX_TAPS, "one splat entry per thread");
   __shared__ FitShared sh;
   const unsigned rank = target_rank<CL>();
   const int b = A.order[blockIdx.x / CL];
