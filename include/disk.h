@@ -394,7 +394,8 @@ int disk_fit_resume(const float *d_targets, const int *sizes, int batch, int L, 
 /* Launch-configuration autotuner of disk_fit: times the persistent fit kernel
  * in each built configuration -- 256, 512 or 1024 threads per CTA, and one
  * CTA or a thread-block cluster of 2 or 4 CTAs (on as many SMs) per target --
- * for a few steps each from the radial initialisation on this batch, and
+ * for a few steps each from the sparse-sampling initialisation (seed 0) on
+ * this batch, and
  * records the fastest for every later disk_fit with the same L, T and largest
  * target size (in 32-pixel buckets); without a recorded choice disk_fit uses
  * 512 threads, one CTA per target.  Synchronises the stream (do not call

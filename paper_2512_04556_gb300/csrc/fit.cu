@@ -334,26 +334,26 @@ __device__ __forceinline__ bool tile_set(const unsigned *mask, int u, int v, int
 }
 
 // sh.tlist <- the tiles of `mask` that meet the box of half-width S, in
-// row-major order; sh.ntiles <- their count.  Run by warp 0; the caller
-// synchronises the CTA before the list is read.
+// row-major order; sh.ntiles <- their count.  Every warp forms the per-row
+// prefix counts with shuffles and places the tiles of the rows it owns; the
+// caller synchronises the CTA before the list is read.
 __device__ void build_tile_list(FitShared &sh, const unsigned *mask, int S) {
-  if (threadIdx.x >= 32) return;
-  const int shift = sh.tshift, G = 16 << shift, lane = threadIdx.x;
+  const int shift = sh.tshift, G = 16 << shift, lane = threadIdx.x & 31;
   const int t0 = max(0, (G - S) >> shift), t1 = min(31, (G + S) >> shift);
   const unsigned cols = ((2u << (t1 - t0)) - 1u) << t0;
-  unsigned w = (lane >= t0 && lane <= t1) ? mask[lane] & cols : 0u;
-  const int c = __popc(w);
-  int off = c;
+  const unsigned w = (lane >= t0 && lane <= t1) ? mask[lane] & cols : 0u;  // row `lane`
+  int off = __popc(w);
   for (int o = 1; o < 32; o <<= 1) {
     const int x = __shfl_up_sync(0xffffffffu, off, o);
     if (lane >= o) off += x;
   }
-  if (lane == 31) sh.ntiles = off;
-  off -= c;
-  while (w) {
-    const int b = __ffs(w) - 1;
-    w &= w - 1u;
-    sh.tlist[off++] = (unsigned short)(lane * 32 + b);
+  if (threadIdx.x == 31) sh.ntiles = off;
+  off -= __popc(w);  // exclusive prefix of row `lane`
+  for (int row = threadIdx.x >> 5; row < 32; row += blockDim.x >> 5) {
+    const unsigned rw = __shfl_sync(0xffffffffu, w, row);
+    const int base = __shfl_sync(0xffffffffu, off, row);
+    if ((rw >> lane) & 1u)
+      sh.tlist[base + __popc(rw & ((1u << lane) - 1u))] = (unsigned short)(row * 32 + lane);
   }
 }
 
@@ -1074,9 +1074,11 @@ extern "C" int disk_fit_autotune(const float *d_targets, const int *sizes, int b
   int kmax = 0;
   for (int b = 0; b < batch; ++b) kmax = std::max(kmax, sizes[b]);
   for (int c = 0; c < (int)(sizeof(kFitConfigs) / sizeof(int)) && rc == DISK_OK; ++c) {
-    // same start for every candidate: the radial initialisation, then 12
-    // steps (enough for the ranking to follow that of a full fit)
-    rc = run_fit(d_targets, sizes, batch, L, T, 0, 1e-3f, 1e-4f, 1, loss, eps, 0, theta, nullptr,
+    // same start for every candidate: the sparse-sampling initialisation,
+    // whose first layer spreads over the target's support as a fitted one
+    // does (the compact Eq. 6 rings make the sparse sweeps unrepresentatively
+    // cheap), then 12 steps (enough for the ranking to follow a full fit's)
+    rc = run_fit(d_targets, sizes, batch, L, T, 0, 1e-3f, 1e-4f, 2, loss, eps, 0, theta, nullptr,
                  nullptr, nullptr, 0, s, kFitConfigs[c]);
     if (rc) break;
     cudaEventRecord(e0, s);
