@@ -259,7 +259,6 @@ struct FitShared {
   // pmask[l-1]: this CTA's marks of them from the sweep of layer l-1
   unsigned pmask[DISK_MAX_LAYERS - 1][32];
   unsigned cmask[DISK_MAX_LAYERS - 1][32];
-  unsigned tmask[32];
   unsigned short tlist[32 * 32];  // the current sweep's tiles, row-major
   int ntiles;
   int tshift;  // tile side 1 << tshift
@@ -333,15 +332,16 @@ __device__ __forceinline__ bool tile_set(const unsigned *mask, int u, int v, int
   return (mask[(v + G) >> shift] >> ((u + G) >> shift)) & 1u;
 }
 
-// sh.tlist <- the tiles of `mask` that meet the box of half-width S, in
-// row-major order; sh.ntiles <- their count.  Every warp forms the per-row
-// prefix counts with shuffles and places the tiles of the rows it owns; the
-// caller synchronises the CTA before the list is read.
-__device__ void build_tile_list(FitShared &sh, const unsigned *mask, int S) {
+// sh.tlist <- the tiles of a mask that meet the box of half-width S, in
+// row-major order; sh.ntiles <- their count.  Every warp calls it with the
+// mask's row `lane` in `row_word`, forms the per-row prefix counts with
+// shuffles and places the tiles of the rows it owns; the caller synchronises
+// the CTA before the list is read (and after the previous list's last read).
+__device__ void build_tile_list(FitShared &sh, unsigned row_word, int S) {
   const int shift = sh.tshift, G = 16 << shift, lane = threadIdx.x & 31;
   const int t0 = max(0, (G - S) >> shift), t1 = min(31, (G + S) >> shift);
   const unsigned cols = ((2u << (t1 - t0)) - 1u) << t0;
-  const unsigned w = (lane >= t0 && lane <= t1) ? mask[lane] & cols : 0u;  // row `lane`
+  const unsigned w = (lane >= t0 && lane <= t1) ? row_word & cols : 0u;  // row `lane`
   int off = __popc(w);
   for (int o = 1; o < 32; o <<= 1) {
     const int x = __shfl_up_sync(0xffffffffu, off, o);
@@ -369,14 +369,13 @@ __device__ __forceinline__ bool tile_item(const FitShared &sh, int w, int items,
   return abs(u) <= S && abs(v) <= S;
 }
 
-// sh.tmask <- the tiles where dL/dI_l is read, l >= 2: D_2 = C_1 (the
-// closed-form gradients of the first two layers read it within the second
-// layer's reach of the splats) and D_{m+1} = C_m (the tap gradients of layer
-// m) | D_m dilated by layer m's reach in tiles (its adjoint's reads).  Run by
-// warp 0; the caller synchronises the CTA.
-__device__ void needed_tiles(FitShared &sh, int l) {
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x, shift = sh.tshift;
+// Row `lane` of the mask of tiles where dL/dI_l is read, l >= 2: D_2 = C_1
+// (the closed-form gradients of the first two layers read it within the
+// second layer's reach of the splats) and D_{m+1} = C_m (the tap gradients of
+// layer m) | D_m dilated by layer m's reach in tiles (its adjoint's reads).
+// Computed by every warp in registers.
+__device__ unsigned needed_row(const FitShared &sh, int l) {
+  const int lane = threadIdx.x & 31, shift = sh.tshift;
   unsigned d = sh.cmask[0][lane];
   for (int m = 2; m < l; ++m) {
     const int r = (sh.ext[m].H + (1 << shift) - 1) >> shift;
@@ -391,7 +390,7 @@ __device__ void needed_tiles(FitShared &sh, int l) {
     }
     d = e | sh.cmask[m - 1][lane];
   }
-  sh.tmask[lane] = d;
+  return d;
 }
 
 // taps (pixels) from normalised parameters; layer extents from the taps.
@@ -573,17 +572,23 @@ __device__ float forward_loss(FitShared &sh, const FitArgs &A, const FitMeta &m,
     float *dst = act[l + 1];
     unsigned *cm = sh.cmask[l - 1];
     // layer l's candidate tiles: for l >= 2 the union of the cluster's marks
-    // from the previous sweep (published by the barrier that ended it)
-    if (l >= 2 && threadIdx.x < 32) {
-      unsigned w = 0u;
-      for (unsigned r = 0; r < (unsigned)CL; ++r) w |= rank_ptr_u<CL>(sh.pmask[l - 1], r)[threadIdx.x];
-      cm[threadIdx.x] = w;
+    // from the previous sweep (published by the barrier that ended it),
+    // formed by every warp in registers
+    unsigned crow;
+    if (l >= 2) {
+      crow = 0u;
+      for (unsigned r = 0; r < (unsigned)CL; ++r)
+        crow |= rank_ptr_u<CL>(sh.pmask[l - 1], r)[threadIdx.x & 31];
+    } else {
+      crow = cm[threadIdx.x & 31];
     }
     const bool mark = l + 1 < L;  // this sweep marks the next layer's candidates
-    if (mark && threadIdx.x < 32) sh.pmask[l][threadIdx.x] = 0u;
+    if (threadIdx.x < 32) {
+      cm[threadIdx.x] = crow;
+      if (mark) sh.pmask[l][threadIdx.x] = 0u;
+    }
     prepare_taps(sh.pt, sh.taps + l * T, T, sh.ext[l].H, 1.f, R);
-    __syncthreads();
-    build_tile_list(sh, cm, S);
+    build_tile_list(sh, crow, S);  // the previous list's reads ended at the cluster barrier
     __syncthreads();
     const int items = sh.ntiles << (2 * shift), Hn = mark ? sh.ext[l + 1].H : 0;
     for (int w = tid; w < ((items + 31) & ~31); w += nthr) {  // whole warps
@@ -672,7 +677,7 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     // wi = c * T + i is done by global warp wi mod nwt, which keeps its sums
     // in its own CTA's part[] slot wi; they are added in chunk order below.
     // only layer l's candidate tiles: elsewhere every corner it reads is 0
-    build_tile_list(sh, sh.cmask[l - 1], S);
+    build_tile_list(sh, sh.cmask[l - 1][lane], S);
     __syncthreads();
     const int items = sh.ntiles << (2 * sh.tshift);
     const int chunks = max(1, nwt / T);
@@ -706,9 +711,9 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     // (reads G like the tap gradients above, writes the other plane), only
     // on the tiles where it is read later
     prepare_taps(sh.pt, sh.taps + l * T, T, halo, -1.f, R);
-    needed_tiles(sh, l);
+    const unsigned drow = needed_row(sh, l);
     __syncthreads();  // the tap gradients are done with the list
-    build_tile_list(sh, sh.tmask, sh.ext[l - 1].S);
+    build_tile_list(sh, drow, sh.ext[l - 1].S);
     __syncthreads();
     {
       const int Sa = sh.ext[l - 1].S, na = sh.ntiles << (2 * sh.tshift);
@@ -729,11 +734,20 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     target_sync<CL>();
     for (int j = threadIdx.x; j < T * 3; j += blockDim.x) {
       const int i = j / 3, k = j % 3;
-      float acc = 0.f;
-      for (int c = 0; c < chunks; ++c) {
+      auto val = [&](int c) {
         const int wi = c * T + i;
-        acc += rank_ptr<CL>(part, (unsigned)((wi % nwt) / nw))[(size_t)wi * 3 + k];
+        return rank_ptr<CL>(part, (unsigned)((wi % nwt) / nw))[(size_t)wi * 3 + k];
+      };
+      float acc = 0.f;
+      int c = 0;
+      for (; c + 4 <= chunks; c += 4) {  // four reads in flight, added in chunk order
+        const float a0 = val(c), a1 = val(c + 1), a2 = val(c + 2), a3 = val(c + 3);
+        acc += a0;
+        acc += a1;
+        acc += a2;
+        acc += a3;
       }
+      for (; c < chunks; ++c) acc += val(c);
       sh.g[(size_t)l * T * 3 + j] = acc;
     }
     float *t = G; G = Gn; Gn = t;
