@@ -27,7 +27,6 @@
 // all but the largest targets); the canvas half-width bounds every support
 // the clamp allows.
 #include <algorithm>
-#include <climits>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -250,18 +249,10 @@ struct FitShared {
   PreparedTaps pt;  // the layer being swept
   float red[kFitMaxWarps];
   float closs;  // this CTA's share of the loss
-  // the first layer's non-zero output pixels (closed form)
+  // the first layer's non-zero output pixels (closed form, rank 0 only)
   int splat_pix[4 * DISK_MAX_TAPS];
   float splat_val[4 * DISK_MAX_TAPS];
   int nsplat;
-  // sparse sweeps: tile masks (one word per row of the 32 x 32 tile grid).
-  // cmask[l-1]: the tiles of layer l's output box that can be non-zero;
-  // pmask[l-1]: this CTA's marks of them from the sweep of layer l-1
-  unsigned pmask[DISK_MAX_LAYERS - 1][32];
-  unsigned cmask[DISK_MAX_LAYERS - 1][32];
-  unsigned short tlist[32 * 32];  // the current sweep's tiles, row-major
-  int ntiles;
-  int tshift;  // tile side 1 << tshift
   // per-(chunk, tap) partial tap gradients of the warps of this CTA, two
   // buffers used by alternate layers
   static constexpr int kPart = 3 * (kFitMaxWarps * kFitMaxCluster > DISK_MAX_TAPS
@@ -298,101 +289,6 @@ __device__ __forceinline__ const float *rank_ptr(const float *p, unsigned r) {
   return cg::this_cluster().map_shared_rank(const_cast<float *>(p), r);
 }
 
-template <int CL>
-__device__ __forceinline__ const unsigned *rank_ptr_u(const unsigned *p, unsigned r) {
-  if (CL == 1) return p;
-  return cg::this_cluster().map_shared_rank(const_cast<unsigned *>(p), r);
-}
-
-// ---- sparse sweeps -------------------------------------------------------------
-// For the non-convex targets of a fit the canvases are sparse: the first
-// layer's output is T splats and every later layer spreads its input only by
-// its reach.  So each sweep visits only the tiles of its box that can hold a
-// non-zero value.  Tiles are ts x ts (ts = 1 << sh.tshift, at least 8) on a
-// 32 x 32 grid centred on c: tile (tx, ty) covers the offsets
-// [tx ts - G, (tx + 1) ts - G) x [ty ts - G, (ty + 1) ts - G), G = 16 ts, and
-// ts is the smallest that makes the grid cover every box of the step.  A
-// mask holds one 32-bit word per tile row.  Skipped pixels are exact zeros
-// (forward) or are never read (adjoint), so the results are those of the
-// dense sweeps.
-
-// Marks the tiles that meet the offset rectangle [u0, u1] x [v0, v1].
-__device__ __forceinline__ void mark_tiles(unsigned *mask, int u0, int u1, int v0, int v1,
-                                           int shift) {
-  const int G = 16 << shift;
-  const int tx0 = max(0, (u0 + G) >> shift), tx1 = min(31, (u1 + G) >> shift);
-  const int ty0 = max(0, (v0 + G) >> shift), ty1 = min(31, (v1 + G) >> shift);
-  if (tx0 > tx1) return;
-  const unsigned bits = ((2u << (tx1 - tx0)) - 1u) << tx0;
-  for (int ty = ty0; ty <= ty1; ++ty) atomicOr(&mask[ty], bits);
-}
-
-__device__ __forceinline__ bool tile_set(const unsigned *mask, int u, int v, int shift) {
-  const int G = 16 << shift;
-  return (mask[(v + G) >> shift] >> ((u + G) >> shift)) & 1u;
-}
-
-// sh.tlist <- the tiles of a mask that meet the box of half-width S, in
-// row-major order; sh.ntiles <- their count.  Every warp calls it with the
-// mask's row `lane` in `row_word`, forms the per-row prefix counts with
-// shuffles and places the tiles of the rows it owns; the caller synchronises
-// the CTA before the list is read (and after the previous list's last read).
-__device__ void build_tile_list(FitShared &sh, unsigned row_word, int S) {
-  const int shift = sh.tshift, G = 16 << shift, lane = threadIdx.x & 31;
-  const int t0 = max(0, (G - S) >> shift), t1 = min(31, (G + S) >> shift);
-  const unsigned cols = ((2u << (t1 - t0)) - 1u) << t0;
-  const unsigned w = (lane >= t0 && lane <= t1) ? row_word & cols : 0u;  // row `lane`
-  int off = __popc(w);
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, off, o);
-    if (lane >= o) off += x;
-  }
-  if (threadIdx.x == 31) sh.ntiles = off;
-  off -= __popc(w);  // exclusive prefix of row `lane`
-  for (int row = threadIdx.x >> 5; row < 32; row += blockDim.x >> 5) {
-    const unsigned rw = __shfl_sync(0xffffffffu, w, row);
-    const int base = __shfl_sync(0xffffffffu, off, row);
-    if ((rw >> lane) & 1u)
-      sh.tlist[base + __popc(rw & ((1u << lane) - 1u))] = (unsigned short)(row * 32 + lane);
-  }
-}
-
-// Work item w of a sweep over sh.tlist: its pixel offsets (u, v); false past
-// the list or outside the box of half-width S.
-__device__ __forceinline__ bool tile_item(const FitShared &sh, int w, int items, int S, int &u,
-                                          int &v) {
-  if (w >= items) return false;
-  const int shift = sh.tshift, ts = 1 << shift, G = 16 << shift;
-  const int t = sh.tlist[w >> (2 * shift)], q = w & ((1 << (2 * shift)) - 1);
-  u = (t & 31) * ts - G + (q & (ts - 1));
-  v = (t >> 5) * ts - G + (q >> shift);
-  return abs(u) <= S && abs(v) <= S;
-}
-
-// Row `lane` of the mask of tiles where dL/dI_l is read, l >= 2: D_2 = C_1
-// (the closed-form gradients of the first two layers read it within the
-// second layer's reach of the splats) and D_{m+1} = C_m (the tap gradients of
-// layer m) | D_m dilated by layer m's reach in tiles (its adjoint's reads).
-// Computed by every warp in registers.
-__device__ unsigned needed_row(const FitShared &sh, int l) {
-  const int lane = threadIdx.x & 31, shift = sh.tshift;
-  unsigned d = sh.cmask[0][lane];
-  for (int m = 2; m < l; ++m) {
-    const int r = (sh.ext[m].H + (1 << shift) - 1) >> shift;
-    unsigned h = d;
-    for (int k = 1; k <= r; ++k) h |= (d << k) | (d >> k);
-    unsigned e = h;
-    for (int k = 1; k <= r; ++k) {
-      const unsigned dn = __shfl_down_sync(0xffffffffu, h, k);
-      const unsigned up = __shfl_up_sync(0xffffffffu, h, k);
-      if (lane + k < 32) e |= dn;
-      if (lane >= k) e |= up;
-    }
-    d = e | sh.cmask[m - 1][lane];
-  }
-  return d;
-}
-
 // taps (pixels) from normalised parameters; layer extents from the taps.
 __device__ void make_taps(FitShared &sh, int L, int T, float s) {
   for (int j = threadIdx.x; j < L * T; j += blockDim.x)
@@ -408,12 +304,6 @@ __device__ void make_taps(FitShared &sh, int L, int T, float s) {
       const int H = (int)ceilf(mx) + 1;
       S += H;
       if (threadIdx.x == 0) { sh.ext[l].H = H; sh.ext[l].S = S; }
-    }
-    // the tile grid spans [-16 ts, 16 ts) around c: cover the largest box
-    if (threadIdx.x == 0) {
-      int shift = 3;
-      while ((16 << shift) <= S) ++shift;
-      sh.tshift = shift;
     }
   }
   __syncthreads();
@@ -431,26 +321,19 @@ __device__ void make_taps(FitShared &sh, int L, int T, float s) {
 // list (entry k = 4i + e: pixel splat_pix[k], and in splat_val[k] the pixel's
 // value at its first entry, 0 at repeated ones); only the CTA with `write`
 // (the cluster's rank 0) writes the plane, which the caller's barrier
-// publishes.  Every CTA also marks the second layer's candidate tiles: those
-// within its reach of a splat.  One entry per thread: every fit CTA has at
-// least 4 * DISK_MAX_TAPS threads.
-__device__ void splat_first_layer(FitShared &sh, float *dst, int R, int L, int T, bool write) {
+// publishes.  One entry per thread: every fit CTA has at least
+// 4 * DISK_MAX_TAPS threads.
+__device__ void splat_first_layer(FitShared &sh, float *dst, int R, int T, bool write) {
   const int N = 2 * R + 1, n = 4 * T, k = threadIdx.x;
   prepare_taps(sh.pt, sh.taps, T, sh.ext[0].H, 1.f, R);
   if (write)
     for (int j = threadIdx.x; j < sh.nsplat; j += blockDim.x) dst[sh.splat_pix[j]] = 0.f;
-  if (k < 32) sh.cmask[0][k] = 0u;
   __syncthreads();
   if (k < n) {
     const int i = k >> 2, ex = k & 1, ey = (k >> 1) & 1;
     const float4 w = sh.pt.w[i];
-    const int p = R * N + R - sh.pt.off[i] - ey * N - ex;
-    sh.splat_pix[k] = p;
+    sh.splat_pix[k] = R * N + R - sh.pt.off[i] - ey * N - ex;
     sh.splat_val[k] = ey ? (ex ? w.w : w.z) : (ex ? w.y : w.x);
-    if (L >= 2) {
-      const int u = p % N - R, v = p / N - R, H = sh.ext[1].H;
-      mark_tiles(sh.cmask[0], u - H, u + H, v - H, v + H, sh.tshift);
-    }
   }
   __syncthreads();
   float acc = 0.f;
@@ -564,67 +447,15 @@ __device__ float forward_loss(FitShared &sh, const FitArgs &A, const FitMeta &m,
                               float *gL, const float *tgt, unsigned rank) {
   const int L = A.L, T = A.T, R = m.R, N = 2 * R + 1, K = m.K, h = (K - 1) / 2;
   const int tid = (int)rank * blockDim.x + threadIdx.x, nthr = blockDim.x * CL;
-  splat_first_layer(sh, act[1], R, L, T, rank == 0);
+  splat_first_layer(sh, act[1], R, T, rank == 0);
   target_sync<CL>();
   for (int l = 1; l < L; ++l) {
-    const int S = sh.ext[l].S, shift = sh.tshift;
-    const float *src = act[l];
-    float *dst = act[l + 1];
-    unsigned *cm = sh.cmask[l - 1];
-    // layer l's candidate tiles: for l >= 2 the union of the cluster's marks
-    // from the previous sweep (published by the barrier that ended it),
-    // formed by every warp in registers
-    unsigned crow;
-    if (l >= 2) {
-      crow = 0u;
-      for (unsigned r = 0; r < (unsigned)CL; ++r)
-        crow |= rank_ptr_u<CL>(sh.pmask[l - 1], r)[threadIdx.x & 31];
-    } else {
-      crow = cm[threadIdx.x & 31];
-    }
-    const bool mark = l + 1 < L;  // this sweep marks the next layer's candidates
-    if (threadIdx.x < 32) {
-      cm[threadIdx.x] = crow;
-      if (mark) sh.pmask[l][threadIdx.x] = 0u;
-    }
+    const int S = sh.ext[l].S;
     prepare_taps(sh.pt, sh.taps + l * T, T, sh.ext[l].H, 1.f, R);
-    build_tile_list(sh, crow, S);  // the previous list's reads ended at the cluster barrier
     __syncthreads();
-    const int items = sh.ntiles << (2 * shift), Hn = mark ? sh.ext[l + 1].H : 0;
-    for (int w = tid; w < ((items + 31) & ~31); w += nthr) {  // whole warps
-      int u = 0, v = 0;
-      const bool ok = tile_item(sh, w, items, S, u, v);
-      float acc = 0.f;
-      if (ok) {
-        const float *base = src + (R + v) * N + (R + u);
-        for (int i = 0; i < T; ++i) {
-          const float4 wt = sh.pt.w[i];
-          const float *q = base + sh.pt.off[i];
-          acc += wt.x * q[0] + wt.y * q[1] + wt.z * q[N] + wt.w * q[N + 1];
-        }
-        dst[(R + v) * N + (R + u)] = acc;
-      }
-      if (mark) {
-        // the next layer reads this output within its reach: mark the tiles
-        // around the warp's non-zero outputs
-        const bool nz = ok && acc != 0.f;
-        if (__any_sync(0xffffffffu, nz)) {
-          const int u0 = __reduce_min_sync(0xffffffffu, nz ? u : INT_MAX);
-          const int u1 = __reduce_max_sync(0xffffffffu, nz ? u : INT_MIN);
-          const int v0 = __reduce_min_sync(0xffffffffu, nz ? v : INT_MAX);
-          const int v1 = __reduce_max_sync(0xffffffffu, nz ? v : INT_MIN);
-          if ((threadIdx.x & 31) == 0) mark_tiles(sh.pmask[l], u0 - Hn, u1 + Hn, v0 - Hn, v1 + Hn, shift);
-        }
-      }
-    }
-    // the box's pixels in the other tiles are zero
-    const int side = 2 * S + 1;
-    for (int j = tid; j < side * side; j += nthr) {
-      const int v = j / side - S, u = j % side - S;
-      if (!tile_set(cm, u, v, shift)) dst[(R + v) * N + (R + u)] = 0.f;
-    }
+    canvas_layer(act[l], act[l + 1], R, S, sh.pt, T, tid, nthr);
     const int reach = (l + 1 < L) ? S + 2 * sh.ext[l + 1].H : max(S, h);
-    zero_frame(dst, R, S, reach, tid, nthr);  // disjoint from the layer's box
+    zero_frame(act[l + 1], R, S, reach, tid, nthr);  // disjoint from the layer's box
     target_sync<CL>();
   }
   const int bx = max(sh.ext[L - 1].S, h);
@@ -676,10 +507,6 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     // every chunks-th row of the support box, lanes over its pixels.  Unit
     // wi = c * T + i is done by global warp wi mod nwt, which keeps its sums
     // in its own CTA's part[] slot wi; they are added in chunk order below.
-    // only layer l's candidate tiles: elsewhere every corner it reads is 0
-    build_tile_list(sh, sh.cmask[l - 1][lane], S);
-    __syncthreads();
-    const int items = sh.ntiles << (2 * sh.tshift);
     const int chunks = max(1, nwt / T);
     for (int wi = gwarp; wi < T * chunks; wi += nwt) {
       const int i = wi % T, c = wi / T;
@@ -687,19 +514,19 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
       float fx, fy;
       const int nx = min(max(split_floor(t.x, fx), -halo), halo - 1);
       const int ny = min(max(split_floor(t.y, fy), -halo), halo - 1);
-      const int off = ny * N + nx;
       float gw = 0.f, gdx = 0.f, gdy = 0.f;
-      for (int w = c * 32 + lane; w < items; w += chunks * 32) {
-        int u, v;
-        if (!tile_item(sh, w, items, S, u, v)) continue;
-        const int p = (R + v) * N + (R + u);
-        const float g = G[p];
-        const float *q = prev + p + off;
-        const float a = q[0], bq = q[1], cq = q[N], d = q[N + 1];
-        const float top = a + fx * (bq - a), bot = cq + fx * (d - cq);
-        gw += g * (top + fy * (bot - top));
-        gdx += g * ((1.f - fy) * (bq - a) + fy * (d - cq));
-        gdy += g * (bot - top);
+      for (int v = -S + c; v <= S; v += chunks) {
+        const float *grow = G + (R + v) * N + R;
+        const float *prow = prev + (R + v + ny) * N + R + nx;
+        for (int u = -S + lane; u <= S; u += 32) {
+          const float g = grow[u];
+          const float *q = prow + u;
+          const float a = q[0], bq = q[1], cq = q[N], d = q[N + 1];
+          const float top = a + fx * (bq - a), bot = cq + fx * (d - cq);
+          gw += g * (top + fy * (bot - top));
+          gdx += g * ((1.f - fy) * (bq - a) + fy * (d - cq));
+          gdy += g * (bot - top);
+        }
       }
       gw = warp_sum(gw); gdx = warp_sum(gdx); gdy = warp_sum(gdy);
       if (lane == 0) {
@@ -708,28 +535,10 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
       }
     }
     // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
-    // (reads G like the tap gradients above, writes the other plane), only
-    // on the tiles where it is read later
+    // (reads G like the tap gradients above, writes the other plane)
     prepare_taps(sh.pt, sh.taps + l * T, T, halo, -1.f, R);
-    const unsigned drow = needed_row(sh, l);
-    __syncthreads();  // the tap gradients are done with the list
-    build_tile_list(sh, drow, sh.ext[l - 1].S);
     __syncthreads();
-    {
-      const int Sa = sh.ext[l - 1].S, na = sh.ntiles << (2 * sh.tshift);
-      for (int w = tid; w < na; w += nthr) {
-        int u, v;
-        if (!tile_item(sh, w, na, Sa, u, v)) continue;
-        const float *base = G + (R + v) * N + (R + u);
-        float acc = 0.f;
-        for (int i = 0; i < T; ++i) {
-          const float4 wt = sh.pt.w[i];
-          const float *q = base + sh.pt.off[i];
-          acc += wt.x * q[0] + wt.y * q[1] + wt.z * q[N] + wt.w * q[N + 1];
-        }
-        Gn[(R + v) * N + (R + u)] = acc;
-      }
-    }
+    canvas_layer(G, Gn, R, sh.ext[l - 1].S, sh.pt, T, tid, nthr);
     // the partial sums and the adjoint plane are complete everywhere
     target_sync<CL>();
     for (int j = threadIdx.x; j < T * 3; j += blockDim.x) {
@@ -1090,8 +899,7 @@ extern "C" int disk_fit_autotune(const float *d_targets, const int *sizes, int b
   for (int c = 0; c < (int)(sizeof(kFitConfigs) / sizeof(int)) && rc == DISK_OK; ++c) {
     // same start for every candidate: the sparse-sampling initialisation,
     // whose first layer spreads over the target's support as a fitted one
-    // does (the compact Eq. 6 rings make the sparse sweeps unrepresentatively
-    // cheap), then 12 steps (enough for the ranking to follow a full fit's)
+    // does, then 12 steps (enough for the ranking to follow a full fit's)
     rc = run_fit(d_targets, sizes, batch, L, T, 0, 1e-3f, 1e-4f, 2, loss, eps, 0, theta, nullptr,
                  nullptr, nullptr, 0, s, kFitConfigs[c]);
     if (rc) break;
