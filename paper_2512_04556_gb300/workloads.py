@@ -128,16 +128,24 @@ def complex_random(L: int, T: int, reach: float, seed: int, nonneg: bool = False
 _SS = (np.arange(4) - 1.5) / 4.0
 
 
-def _grid(K: int):
+def _axis(K: int) -> np.ndarray:
+    """The 4K supersample coordinates along one axis."""
     h = (K - 1) / 2.0
     c = np.arange(K) - h
-    sy = (c[:, None] + _SS[None, :]).reshape(-1)
-    yy, xx = np.meshgrid(sy, sy, indexing="ij")
-    return xx, yy
+    return (c[:, None] + _SS[None, :]).reshape(-1)
+
+
+def _grid(K: int):
+    """(xx, yy) as a row [1, 4K] and a column [4K, 1] that broadcast to the
+    supersample grid: every grid expression below is evaluated per element
+    exactly as on full arrays, without materialising them."""
+    s = _axis(K)
+    return s[None, :], s[:, None]
 
 
 def _coverage(inside: np.ndarray, K: int) -> np.ndarray:
-    cov = inside.reshape(K, 4, K, 4).mean(axis=(1, 3))
+    # the mean of each pixel's 16 samples: an integer count / 16, exact
+    cov = inside.reshape(K, 4, K, 4).sum(axis=(1, 3), dtype=np.int32) / 16.0
     s = cov.sum()
     if s <= 0:
         cov = np.zeros((K, K))
@@ -172,7 +180,7 @@ def gaussian(sigma: float, K: int | None = None) -> np.ndarray:
     over each pixel, unit sum, odd size 2 ceil(3 sigma) + 1."""
     K = K or 2 * int(math.ceil(3.0 * sigma)) + 1
     xx, yy = _grid(K)
-    g = np.exp(-(xx * xx + yy * yy) / (2.0 * sigma * sigma))
+    g = np.exp(-(xx * xx + yy * yy) / (2.0 * sigma * sigma))  # [4K, 4K] by broadcasting
     g = g.reshape(K, 4, K, 4).mean(axis=(1, 3))
     return g / g.sum()
 
@@ -244,17 +252,24 @@ def ring(radius: float, width: float, K: int | None = None) -> np.ndarray:
 def polygon(verts: np.ndarray, K: int) -> np.ndarray:
     """Even-odd fill of a closed polygon with vertices [n][2] (x, y) about the
     kernel centre."""
-    xx, yy = _grid(K)
-    inside = np.zeros(xx.shape, dtype=bool)
+    # A sample (x, y) is inside when an odd number of edges cross its row y
+    # at some xint > x.  Per edge, the rows it crosses and where; the samples
+    # of a row left of a crossing are a prefix (the axis is ascending), so the
+    # count per sample is a running sum of the crossings' prefix lengths.
+    s = _axis(K)
+    M = len(s)
+    at = np.zeros((M, M + 1), dtype=np.int32)  # crossings per (row, prefix length)
     n = len(verts)
     for i in range(n):
         x1, y1 = verts[i]
         x2, y2 = verts[(i + 1) % n]
-        cond = (y1 > yy) != (y2 > yy)
-        with np.errstate(divide="ignore", invalid="ignore"):
-            xint = (x2 - x1) * (yy - y1) / (y2 - y1) + x1
-        inside ^= cond & (xx < xint)
-    return _coverage(inside, K)
+        rows = np.nonzero((y1 > s) != (y2 > s))[0]
+        if rows.size == 0:
+            continue
+        xint = (x2 - x1) * (s[rows] - y1) / (y2 - y1) + x1
+        np.add.at(at, (rows, np.searchsorted(s, xint, side="left")), 1)
+    count = np.cumsum(at[:, ::-1], axis=1)[:, ::-1]  # crossings with prefix length >= m
+    return _coverage((count[:, 1:] & 1).astype(bool), K)
 
 
 def star(points: int, r_out: float, r_in: float, phase: float, K: int) -> np.ndarray:
