@@ -37,11 +37,16 @@ def _theta_away_from_integers(targets, L, T, seed):
 
 
 @pytest.mark.parametrize("loss,eps", [(0, 0.0), (1, 1e-4)])
-def test_loss_and_gradient_match_oracle(torch_cuda, loss, eps):
+@pytest.mark.parametrize("L,T", [(1, 8), (2, 5), (3, 8), (4, 16), (6, 12)])
+def test_loss_and_gradient_match_oracle(torch_cuda, loss, eps, L, T):
+    """The first layer's closed-form gradients (four pixels per tap; from
+    dL/dI_1 directly at L = 1, through the second layer's adjoint otherwise),
+    the second layer's (sums over the first layer's splats) and the swept
+    layers' against the FP64 gradient."""
     torch = torch_cuda
     from paper_2512_04556_gb300 import disk
     tg = _targets(6, 7, 31)
-    th = _theta_away_from_integers(tg, 3, 8, 1)
+    th = _theta_away_from_integers(tg, L, T, 1)
     packed, sizes = disk.pack_targets(tg)
     l, g = disk.fit_loss_grad(packed, sizes, torch.from_numpy(th).cuda(), loss=loss, eps=eps)
     torch.cuda.synchronize()
