@@ -255,7 +255,7 @@ struct FitShared {
   int nsplat;
   // per-(chunk, tap) partial tap gradients of the warps of this CTA, two
   // buffers used by alternate layers
-  static constexpr int kPart = 3 * (kFitMaxWarps * kFitMaxCluster > DISK_MAX_TAPS
+  static constexpr int kPart = 6 * (kFitMaxWarps * kFitMaxCluster > DISK_MAX_TAPS
                                         ? kFitMaxWarps * kFitMaxCluster
                                         : DISK_MAX_TAPS);
   float part[2 * kPart];
@@ -502,36 +502,51 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     // this layer's partial-sum buffer: the other one may still be read by
     // the cluster's CTAs summing the previous layer
     float *part = sh.part + (l & 1) * FitShared::kPart;
-    // dL/dw, dL/do of every tap of layer l: `chunks` warps of the cluster
-    // per tap (every warp works when T is below the warp count), each over
-    // every chunks-th row of the support box, lanes over its pixels.  Unit
-    // wi = c * T + i is done by global warp wi mod nwt, which keeps its sums
-    // in its own CTA's part[] slot wi; they are added in chunk order below.
-    const int chunks = max(1, nwt / T);
-    for (int wi = gwarp; wi < T * chunks; wi += nwt) {
-      const int i = wi % T, c = wi / T;
-      const float4 t = sh.taps[l * T + i];
-      float fx, fy;
-      const int nx = min(max(split_floor(t.x, fx), -halo), halo - 1);
-      const int ny = min(max(split_floor(t.y, fy), -halo), halo - 1);
-      float gw = 0.f, gdx = 0.f, gdy = 0.f;
+    // dL/dw, dL/do of every tap of layer l, taps in pairs (one read of G
+    // serves both): `chunks` warps of the cluster per pair (every warp works
+    // when the pairs are fewer than the warps), each over every chunks-th row
+    // of the support box, lanes over its pixels.  Unit wi = c * T2 + p is
+    // done by global warp wi mod nwt, which keeps its sums in its own CTA's
+    // part[] slot wi; they are added in chunk order below.  An odd T's last
+    // pair repeats its tap; the repeat's sums are not used.
+    const int T2 = (T + 1) / 2;
+    const int chunks = max(1, nwt / T2);
+    for (int wi = gwarp; wi < T2 * chunks; wi += nwt) {
+      const int ip = wi % T2, c = wi / T2;
+      const int i0 = 2 * ip, i1 = min(2 * ip + 1, T - 1);
+      const float4 t0 = sh.taps[l * T + i0], t1 = sh.taps[l * T + i1];
+      float fx0, fy0, fx1, fy1;
+      const int nx0 = min(max(split_floor(t0.x, fx0), -halo), halo - 1);
+      const int ny0 = min(max(split_floor(t0.y, fy0), -halo), halo - 1);
+      const int nx1 = min(max(split_floor(t1.x, fx1), -halo), halo - 1);
+      const int ny1 = min(max(split_floor(t1.y, fy1), -halo), halo - 1);
+      const int off0 = ny0 * N + nx0, off1 = ny1 * N + nx1;
+      float gw0 = 0.f, gdx0 = 0.f, gdy0 = 0.f, gw1 = 0.f, gdx1 = 0.f, gdy1 = 0.f;
       for (int v = -S + c; v <= S; v += chunks) {
         const float *grow = G + (R + v) * N + R;
-        const float *prow = prev + (R + v + ny) * N + R + nx;
+        const float *prow = prev + (R + v) * N + R;
         for (int u = -S + lane; u <= S; u += 32) {
           const float g = grow[u];
-          const float *q = prow + u;
-          const float a = q[0], bq = q[1], cq = q[N], d = q[N + 1];
-          const float top = a + fx * (bq - a), bot = cq + fx * (d - cq);
-          gw += g * (top + fy * (bot - top));
-          gdx += g * ((1.f - fy) * (bq - a) + fy * (d - cq));
-          gdy += g * (bot - top);
+          const float *q = prow + u + off0;
+          const float a0 = q[0], b0 = q[1], c0 = q[N], d0 = q[N + 1];
+          const float *r = prow + u + off1;
+          const float a1 = r[0], b1 = r[1], c1 = r[N], d1 = r[N + 1];
+          const float top0 = a0 + fx0 * (b0 - a0), bot0 = c0 + fx0 * (d0 - c0);
+          gw0 += g * (top0 + fy0 * (bot0 - top0));
+          gdx0 += g * ((1.f - fy0) * (b0 - a0) + fy0 * (d0 - c0));
+          gdy0 += g * (bot0 - top0);
+          const float top1 = a1 + fx1 * (b1 - a1), bot1 = c1 + fx1 * (d1 - c1);
+          gw1 += g * (top1 + fy1 * (bot1 - top1));
+          gdx1 += g * ((1.f - fy1) * (b1 - a1) + fy1 * (d1 - c1));
+          gdy1 += g * (bot1 - top1);
         }
       }
-      gw = warp_sum(gw); gdx = warp_sum(gdx); gdy = warp_sum(gdy);
+      gw0 = warp_sum(gw0); gdx0 = warp_sum(gdx0); gdy0 = warp_sum(gdy0);
+      gw1 = warp_sum(gw1); gdx1 = warp_sum(gdx1); gdy1 = warp_sum(gdy1);
       if (lane == 0) {
-        float *pp = part + (size_t)wi * 3;
-        pp[0] = gdx * t.z; pp[1] = gdy * t.z; pp[2] = gw;
+        float *pp = part + (size_t)wi * 6;
+        pp[0] = gdx0 * t0.z; pp[1] = gdy0 * t0.z; pp[2] = gw0;
+        pp[3] = gdx1 * t1.z; pp[4] = gdy1 * t1.z; pp[5] = gw1;
       }
     }
     // adjoint plane dL/dI_{l-1} on the support of I_{l-1}: gather at -o
@@ -542,10 +557,10 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
     // the partial sums and the adjoint plane are complete everywhere
     target_sync<CL>();
     for (int j = threadIdx.x; j < T * 3; j += blockDim.x) {
-      const int i = j / 3, k = j % 3;
+      const int i = j / 3, k = j % 3, ip = i / 2, h = i % 2;
       auto val = [&](int c) {
-        const int wi = c * T + i;
-        return rank_ptr<CL>(part, (unsigned)((wi % nwt) / nw))[(size_t)wi * 3 + k];
+        const int wi = c * T2 + ip;
+        return rank_ptr<CL>(part, (unsigned)((wi % nwt) / nw))[(size_t)wi * 6 + h * 3 + k];
       };
       float acc = 0.f;
       int c = 0;
