@@ -522,14 +522,18 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
       const int ny1 = min(max(split_floor(t1.y, fy1), -halo), halo - 1);
       const int off0 = ny0 * N + nx0, off1 = ny1 * N + nx1;
       float gw0 = 0.f, gdx0 = 0.f, gdy0 = 0.f, gw1 = 0.f, gdx1 = 0.f, gdy1 = 0.f;
-      for (int v = -S + c; v <= S; v += chunks) {
-        const float *grow = G + (R + v) * N + R;
-        const float *prow = prev + (R + v) * N + R;
-        for (int u = -S + lane; u <= S; u += 32) {
-          const float g = grow[u];
-          const float *q = prow + u + off0;
+      // the box's pixels in row-major order, 32 per warp pass, every chunks-th
+      // pass: no lane idles at a row's end; (u, v) advanced, not divided
+      const int side = 2 * S + 1, npx = side * side, step = chunks * 32;
+      const int dv = step / side, du = step - dv * side;
+      int j = c * 32 + lane, v = j / side - S, u = j - (v + S) * side - S;
+      for (; j < npx; j += step) {
+        {
+          const int p = (R + v) * N + (R + u);
+          const float g = G[p];
+          const float *q = prev + p + off0;
           const float a0 = q[0], b0 = q[1], c0 = q[N], d0 = q[N + 1];
-          const float *r = prow + u + off1;
+          const float *r = prev + p + off1;
           const float a1 = r[0], b1 = r[1], c1 = r[N], d1 = r[N + 1];
           const float top0 = a0 + fx0 * (b0 - a0), bot0 = c0 + fx0 * (d0 - c0);
           gw0 += g * (top0 + fy0 * (bot0 - top0));
@@ -539,6 +543,12 @@ __device__ void backward(FitShared &sh, const FitArgs &A, const FitMeta &m, floa
           gw1 += g * (top1 + fy1 * (bot1 - top1));
           gdx1 += g * ((1.f - fy1) * (b1 - a1) + fy1 * (d1 - c1));
           gdy1 += g * (bot1 - top1);
+        }
+        u += du;
+        v += dv;
+        if (u > S) {
+          u -= side;
+          ++v;
         }
       }
       gw0 = warp_sum(gw0); gdx0 = warp_sum(gdx0); gdy0 = warp_sum(gdy0);
