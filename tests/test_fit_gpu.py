@@ -176,3 +176,28 @@ def _oracle_hist(t, key):
     if key not in _ORACLE_CACHE:
         _ORACLE_CACHE[key] = oracle.fit(t, 4, 16, 60, init=oracle.INIT_SS, seed=5)[1]
     return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("K,L,T", [(257, 4, 16), (33, 8, 64), (21, 16, 32), (1, 2, 4), (3, 1, 1)])
+def test_fit_at_the_size_limits(torch_cuda, K, L, T):
+    """The largest target (K = 257), the largest complexes (L * T = 512, up to
+    16 layers; the splat list then fills 256 threads) and degenerate ones
+    (K = 1, T = 1): loss and gradient against the FP64 oracle, and five Adam
+    steps against the oracle's trajectory."""
+    torch = torch_cuda
+    from paper_2512_04556_gb300 import disk
+    t = wl.ring(max(1.0, (K - 1) / 2 - 2.0), max(1.5, K / 12), K) if K >= 9 else wl.disk(1.0, K)
+    th = _theta_away_from_integers([t], L, T, K + L)
+    packed, sizes = disk.pack_targets([t])
+    l, g = disk.fit_loss_grad(packed, sizes, torch.from_numpy(th).cuda())
+    torch.cuda.synchronize()
+    wl_, wg = oracle.fit_loss(th[0].astype(np.float64), t, 0, 0.0, grad=True)
+    assert abs(float(l[0]) - wl_) <= 1e-4 * abs(wl_)
+    err = np.abs(g.cpu().numpy()[0] - wg).max() / max(np.abs(wg).max(), 1e-30)
+    assert err <= 1e-4, err
+    got, _, hist = disk.fit(packed, sizes, L, T, 5, init=disk.INIT_GIVEN,
+                            theta=torch.from_numpy(th).cuda(), loss_hist=True)
+    want, whist = oracle.fit(t, L, T, 5, init=oracle.INIT_GIVEN, theta0=th[0].astype(np.float64))
+    np.testing.assert_allclose(hist.cpu().numpy()[0], whist, rtol=2e-3)
+    s = max(1.0, (K - 1) / 2)
+    assert np.abs(got.cpu().numpy()[0] - want).max() <= 2e-3 * s
