@@ -14,8 +14,8 @@
 //             H_l = ceil(max |o_l|) + 1 from the current taps; the first
 //             layer in closed form (its output is T bilinear splats);
 //   loss      MSE (or Charbonnier, Eq. 11) over the plane, target zero-padded;
-//   backward  dL/dI_L, then per layer the tap gradients (one warp per tap,
-//             warp-shuffle reductions) and the adjoint plane, which on a
+//   backward  dL/dI_L, then per layer the tap gradients (one warp per pair
+//             of taps, warp-shuffle reductions) and the adjoint plane, which on a
 //             zero-bounded canvas is the same layer applied at -o (the
 //             bilinear tent is symmetric) -- a gather, no atomics; the
 //             first layer's tap gradients in closed form from the four pixels
