@@ -26,6 +26,7 @@ from __future__ import annotations
 import json
 import os
 import struct
+import threading
 import zlib
 
 import numpy as np
@@ -64,7 +65,7 @@ def save(path: str, kind: str, meta: dict, arrays: dict) -> None:
     crc = zlib.crc32(head)
     for b in blobs:
         crc = zlib.crc32(b, crc)
-    tmp = f"{path}.tmp{os.getpid()}"
+    tmp = f"{path}.tmp{os.getpid()}.{threading.get_ident()}"
     with open(tmp, "wb") as f:
         f.write(head)
         for b in blobs:

@@ -122,3 +122,20 @@ def test_network_checkpoint_round_trip_and_checks(tmp_path):
     ck.save(p, "mlp", {"shape": [64, 16, 2, 12], "step": -1}, {"params": params, "m": m, "v": v})
     with pytest.raises(ck.CheckpointError, match="step"):
         ck.load_mlp(p)
+
+
+def test_concurrent_saves_leave_one_whole_file(tmp_path):
+    """Threads saving the same path each write their own temporary file and
+    rename it: the result is one of the saved checkpoints, whole."""
+    import threading
+    p = str(tmp_path / "x.ckpt")
+    arrays = [np.full(5000, k, np.float32) for k in range(8)]
+    ts = [threading.Thread(target=ck.save, args=(p, "demo", {"k": k}, {"a": arrays[k]}))
+          for k in range(8)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    _, meta, a = ck.load(p)
+    assert a["a"].tolist() == arrays[meta["k"]].tolist()
+    assert not [n for n in os.listdir(tmp_path) if ".tmp" in n]
