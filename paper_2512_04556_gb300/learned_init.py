@@ -18,7 +18,6 @@ Pipeline, every numeric step in the library's CUDA kernels:
 from __future__ import annotations
 
 import json
-import math
 import time
 
 import numpy as np
